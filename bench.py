@@ -1,0 +1,338 @@
+"""Benchmark: Gk-mers/s of the k-mer counter on a seeded synthetic workload.
+
+One step = one kc_count (every kernel of the hot path) over the whole read set,
+inputs resident in HBM.  Prints ONE JSON line (rank 0).  See the design doc for the
+byte model behind the roofline figures.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+Under torchrun (N > 1) every rank counts its own replica of the workload on its
+own GPU (no collective in the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gk-mers/s counted (bit-exact vs oracle), % HBM roofline; batched/served vs plain"
+UNIT = "Gk-mers/s"
+DEFAULT_WORKLOAD = "repeats_100mbp_150bp_30x_k31"
+WORKLOAD_DESC = {
+    "uniform_1mbp_100bp_10x_k31": "1 Mbp i.i.d. genome, 100 bp reads, 10x, 0.5% subst, 0.01% N, k=31 canonical",
+    "repeats_100mbp_150bp_30x_k31": "100 Mbp genome (20% from 500 repeat families, Zipf 1.2, 2% divergence), "
+                                    "150 bp reads, 30x, 0.5% subst, k=31 canonical",
+    "long_50mbp_10kbp_20x_k63": "50 Mbp i.i.d. genome, log-normal 10 kbp reads, 20x, 5% errors 60/20/20, k=63 canonical",
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("kc_kernels.cu", "kc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2505_04431_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if taken on this kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(workload, {}).get(kernel)
+        if e and e.get("source_hash") == source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sms, mx, reasons = [], None, set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def kernel_bytes(L, n_reads, K, D, w):
+    """algorithmic bytes per launch of each kernel (byte model)"""
+    packed = L // 4 + L // 8
+    return {
+        "k_pack_count": L + 8 * n_reads + packed,
+        "k_scatter": packed + 8 * n_reads + K * w,
+        "k_fine_hist": K * w,
+        "k_fine_scatter": 2 * K * w,
+        "k_count_emit": K * w + D * (w + 4),
+    }
+
+
+def cpu_baseline(reads, offsets, k, target_s=12.0):
+    """The oracle as it stands, single-threaded, on the first reads of the workload."""
+    import oracle
+    n = len(offsets) - 1
+    m = max(1, n // 2000)
+    while True:
+        o = offsets[:m + 1]
+        r = reads[: int(o[-1])]
+        t0 = time.perf_counter()
+        _, _, nv = oracle.count(r, o, k, True)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or m >= n:
+            return {"value": nv / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"first {m} of {n} reads ({int(o[-1])} bases, {nv} windows), {dt:.1f} s"}
+        m = min(n, int(m * max(2.0, 1.2 * target_s / max(dt, 1e-3))))
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, bounded sample per step."""
+    import oracle
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    reads, offsets, k = synth.workload(args.workload)
+    n = len(offsets) - 1
+    # size one step to ~6 s of CPU work
+    m = max(1, n // 4000)
+    while True:
+        o = offsets[:m + 1]
+        t0 = time.perf_counter()
+        oracle.count(reads[: int(o[-1])], o, k, True)
+        dt = time.perf_counter() - t0
+        if dt >= 1.5 or m >= n:
+            break
+        m = min(n, m * 2)
+    m = min(n, max(1, int(m * 6.0 / max(dt, 1e-3))))
+    o = offsets[:m + 1]
+    r = reads[: int(o[-1])]
+    for _ in range(args.warmup):
+        oracle.count(r, o, k, True)
+    t0 = time.perf_counter()
+    nv = 0
+    for _ in range(args.steps):
+        _, _, nv = oracle.count(r, o, k, True)
+    dt = time.perf_counter() - t0
+    value = nv * args.steps / dt / 1e9
+    sample = f"first {m} of {n} reads ({int(o[-1])} bases, {nv} windows) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64" if k <= 32 else "u128",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, "")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import synth
+    from paper_2505_04431_gb300 import KmerCounter
+    from paper_2505_04431_gb300 import build as kcbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        kcbuild.build()
+    if dist:
+        dist.barrier()
+    reads, offsets, k = synth.workload(args.workload)
+    n_reads, L = len(offsets) - 1, len(reads)
+    stream = torch.cuda.Stream(dev)
+    counter = KmerCounter(device=dev, stream=stream, profile=True)
+    r_dev = torch.from_numpy(reads).to(dev)
+    o_dev = torch.from_numpy(offsets.view(np.int64)).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        res = counter.count(r_dev, o_dev, k, True)
+        out = (res.n, res.n_valid_windows, res.key_words)
+        res.free()
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ktimes = {}
+    launches = 0
+    D = K = kw = 0
+    for _ in range(args.steps):
+        D, K, kw = step()
+        launches += counter.stats()["kernel_launches"]
+        for name, ms in counter.kernel_times():
+            ktimes.setdefault(name, []).append(ms)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = elapsed_ms / args.steps
+    value = K * world * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers: pinned H2D inside the call, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        r_pin = torch.from_numpy(reads).pin_memory()
+        o_pin = torch.from_numpy(offsets.view(np.int64)).pin_memory()
+        keys_h = torch.empty(D * kw, dtype=torch.int64).pin_memory()
+        cnt_h = torch.empty(D, dtype=torch.int32).pin_memory()
+        import ctypes
+        from paper_2505_04431_gb300 import load_library, _check
+        lib = load_library()
+
+        def e2e_step():
+            res = counter.count(r_pin, o_pin, k, True)
+            _check(lib, lib.kc_result_copy_to_host(counter._plan, ctypes.byref(res._res), keys_h.data_ptr(),
+                                                   cnt_h.data_ptr()))
+            out = res.n
+            res.free()
+            return out
+
+        e2e_step()
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": K * world * e2e_steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(L + 8 * (n_reads + 1)), "d2h_bytes_per_step": int(D * (8 * kw + 4)),
+               "steps": e2e_steps}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    w = 8 * kw
+    peak, peak_kind = measured_peaks()
+    kb = kernel_bytes(L, n_reads, K, D, w)
+    avg = {n: sum(v) / len(v) for n, v in ktimes.items()}
+    total_k = sum(avg.values()) or 1.0
+    dom = max((n for n in avg if n in kb), key=lambda n: avg[n])
+    achieved = kb[dom] / (avg[dom] / 1e3) / 1e9
+    B = L + 8 * n_reads + 2 * K * w + D * (w + 4)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dom, args.workload),
+                "alg_bytes_per_launch": kb[dom], "ms_per_launch": avg[dom], "share": avg[dom] / total_k}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64" if kw == 1 else "u128", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""), "k": k, "canonical": True,
+                   "reads": n_reads, "bases": L, "windows": K, "distinct": D,
+                   "l2": f"inputs larger than L2 ({L / 1e9:.2f} GB of reads, {K * w / 1e9:.1f} GB of keys per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": roofline,
+        "path_roofline": {"bytes": B, "achieved": B / (ms_per_step / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": B / (ms_per_step / 1e3) / 1e9 / peak},
+        "kernels_ms": {n: round(v, 4) for n, v in sorted(avg.items(), key=lambda x: -x[1])},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(reads, offsets, k)
+    print(json.dumps(line), flush=True)
+    counter.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

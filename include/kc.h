@@ -1,0 +1,137 @@
+/*
+ * kc.h - C ABI of a single-GPU k-mer counter for NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Section II, problem statement; Algorithm 1, serial counter;
+ * Algorithm 3, FA-BSP counter): given DNA reads, return the ordered array of
+ * {k-mer, count} pairs of all length-k substrings of the reads.
+ *
+ *   - A read is a run of bytes; read i is reads[offsets[i] .. offsets[i+1]).
+ *   - A window of k consecutive bytes inside one read counts iff every byte is
+ *     one of A C G T a c g t (lowercase reads as uppercase).  A window with any
+ *     other byte ('N', junk) is skipped whole; windows never span two reads.
+ *   - The key of a window is the k-digit base-4 number with digits A=0 C=1 G=2
+ *     T=3, first base most significant (Algorithm 1: kmer = (kmer << 2) OR
+ *     Encode(base), keeping the low 2k bits).
+ *   - Canonical mode: key = min(forward value, value of the reverse complement)
+ *     as unsigned integers (the paper counts forward k-mers; canonical form is
+ *     this library's reading for double-stranded reads).
+ *   - Keys are 64-bit for k <= 32 and 128-bit for 33 <= k <= 64 (Section VII
+ *     names 128-bit k-mers as the extension for long reads).
+ *   - Result: distinct keys in strictly ascending unsigned order with their
+ *     occurrence counts (Algorithm 1: Sort, then Accumulate).
+ *
+ * Every function returns a kc_status; no C++ exception crosses this ABI.  On
+ * failure kc_last_error() describes the error (per calling thread).
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KC_OK = 0,
+  KC_EINVAL = 1,     /* bad argument; nothing was launched */
+  KC_ENOMEM = 2,     /* the allocator returned NULL */
+  KC_ECUDA = 3,      /* a CUDA runtime call failed */
+  KC_EOVERFLOW = 4,  /* a count exceeded 2^32 - 1 */
+  KC_ETIMEOUT = 5,   /* a bounded device-side wait gave up (result invalid) */
+  KC_EBUSY = 6       /* the plan is in use by another call */
+} kc_status;
+
+typedef struct kc_plan_s *kc_plan_t;
+
+/* Device memory hooks.  alloc returns a device pointer of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free_ releases it. */
+typedef void *(*kc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*kc_free_fn)(void *ptr, void *stream, void *ctx);
+
+typedef struct {
+  int device;                 /* CUDA device ordinal the plan runs on */
+  void *stream;               /* cudaStream_t for all work; NULL = legacy default stream */
+  kc_alloc_fn alloc;          /* NULL: cudaMallocAsync on `stream` */
+  kc_free_fn free_;           /* NULL: cudaFreeAsync on `stream` */
+  void *alloc_ctx;            /* passed back to alloc / free_ */
+  uint64_t max_device_bytes;  /* 0: no limit; else kc_count fails with KC_ENOMEM above it */
+  uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 4096); 0: chosen from input size */
+  uint32_t block_size_hint;   /* reserved (0) */
+  float table_load;           /* target load of the per-partition count tables; 0: 0.5 */
+  uint32_t table_slots_max;   /* 0: largest table that fits shared memory; smaller values
+                                 (>= 64) force the overflow path, for testing */
+  uint32_t flags;             /* KC_PLAN_* bits */
+} kc_plan_opts;
+
+/* kc_plan_opts.flags: record a CUDA event on the plan's stream after every kernel
+ * launch of kc_count, so kc_last_kernel_times can report each kernel's device time. */
+#define KC_PLAN_PROFILE 1u
+
+typedef struct {
+  uint64_t n;               /* number of distinct keys */
+  uint32_t key_words;       /* 1: keys are uint64[n]; 2: keys are uint64[2n], (lo, hi) per key */
+  void *keys;               /* device pointer, ascending (for key_words 2: by hi, then lo) */
+  uint32_t *counts;         /* device pointer, n counts, each >= 1 */
+  uint64_t n_valid_windows; /* number of windows that counted = sum of counts */
+  uint64_t capacity;        /* entries allocated behind keys / counts (>= n) */
+  void *_owner;             /* library bookkeeping; do not touch */
+} kc_result;
+
+/* Create a plan (device properties, kernel attributes, memory hooks).  The plan
+ * keeps its scratch memory between calls and grows it on demand.
+ * Errors: KC_EINVAL (opts NULL or bad values), KC_ECUDA. */
+kc_status kc_plan(const kc_plan_opts *opts, kc_plan_t *out);
+
+/* Count the k-mers of n_reads reads.
+ *   reads    bytes of all reads, back to back; host or device memory (detected
+ *            with cudaPointerGetAttributes); borrowed until the call returns.
+ *   offsets  n_reads + 1 uint64 offsets into `reads`, offsets[0] == 0,
+ *            non-decreasing; host or device memory.
+ *   k        1..64.   canonical  0: forward keys; nonzero: canonical keys.
+ * On KC_OK, *out holds device buffers owned by the library until kc_free.
+ * The call is synchronous with respect to the plan's stream (it returns after
+ * the result is complete).
+ * Errors: KC_EINVAL (k out of range, NULL pointers, offsets[0] != 0, offsets not
+ * non-decreasing), KC_ENOMEM, KC_ECUDA, KC_EOVERFLOW (a count above 2^32 - 1),
+ * KC_ETIMEOUT (device wait limit hit).  On any error *out is zeroed. */
+kc_status kc_count(kc_plan_t plan, const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, int k,
+                   int canonical, kc_result *out);
+
+/* Release the buffers of a result returned by kc_count (stream-ordered on the
+ * plan's stream).  A zeroed result is accepted.  Errors: KC_EINVAL. */
+kc_status kc_free(kc_plan_t plan, kc_result *res);
+
+/* Copy a result to host memory: keys_host must hold n * key_words uint64,
+ * counts_host n uint32.  Synchronous.  Errors: KC_EINVAL, KC_ECUDA. */
+kc_status kc_result_copy_to_host(kc_plan_t plan, const kc_result *res, uint64_t *keys_host, uint32_t *counts_host);
+
+/* Destroy a plan and its scratch memory.  Results must be freed first. */
+kc_status kc_plan_destroy(kc_plan_t plan);
+
+/* Message for the last error on this thread ("" if none). */
+const char *kc_last_error(void);
+
+/* Launch statistics of the last kc_count on this plan: number of kernel
+ * launches and the coarse/fine partition counts used.  Errors: KC_EINVAL. */
+typedef struct {
+  uint32_t kernel_launches;
+  uint32_t n_partitions;       /* coarse partitions (phase 1) */
+  uint64_t n_fine;             /* fine partitions (one shared-memory table each) */
+  uint64_t n_overflow_fine;    /* fine partitions that needed the overflow path */
+  uint64_t workspace_bytes;    /* scratch currently held by the plan */
+} kc_stats;
+kc_status kc_last_stats(kc_plan_t plan, kc_stats *out);
+
+/* Device time of each kernel launched by the last kc_count on a plan created with
+ * KC_PLAN_PROFILE, measured with CUDA events on the plan's stream.  Fills up to
+ * `max` entries of names (static strings) and ms; *n_out = entries available.
+ * Errors: KC_EINVAL (NULL plan / n_out, or the plan was not created with
+ * KC_PLAN_PROFILE). */
+kc_status kc_last_kernel_times(kc_plan_t plan, uint32_t max, const char **names, float *ms, uint32_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KC_H */

@@ -1,0 +1,258 @@
+"""GB300-native k-mer counter: Python binding of the C ABI in include/kc.h.
+
+This module only marshals arguments: every step of the count runs in the CUDA
+kernels of libkc.so (built in-tree by build.py).  PyTorch provides device
+memory (its caching allocator, through the plan's alloc/free hooks) and the
+current CUDA stream.  There is no CPU fallback: without the built library, or
+without a CUDA device, the calls raise.
+
+    counter = KmerCounter()                       # plan on the current device/stream
+    res = counter.count(reads, offsets, k=31)     # reads: uint8, offsets: uint64 (n_reads + 1)
+    keys, counts = res.to_numpy()                 # ascending keys, their counts
+    res.free()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkc.so")
+
+KC_OK, KC_EINVAL, KC_ENOMEM, KC_ECUDA, KC_EOVERFLOW, KC_ETIMEOUT, KC_EBUSY = range(7)
+STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "KC_EOVERFLOW",
+                5: "KC_ETIMEOUT", 6: "KC_EBUSY"}
+
+# every entry point declared in include/kc.h
+EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
+            "kc_last_error", "kc_last_stats", "kc_last_kernel_times"]
+KC_PLAN_PROFILE = 1
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("alloc", _ALLOC_FN), ("free_", _FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("max_device_bytes", ctypes.c_uint64), ("n_partitions_hint", ctypes.c_uint32),
+                ("block_size_hint", ctypes.c_uint32), ("table_load", ctypes.c_float),
+                ("table_slots_max", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("key_words", ctypes.c_uint32), ("keys", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("n_valid_windows", ctypes.c_uint64),
+                ("capacity", ctypes.c_uint64), ("_owner", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint32), ("n_partitions", ctypes.c_uint32),
+                ("n_fine", ctypes.c_uint64), ("n_overflow_fine", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+class KcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libkc.so and declare its signatures.  Raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libkc.so not found at {path}; build it with paper_2505_04431_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    lib.kc_plan.argtypes = [ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+    lib.kc_plan.restype = i32
+    lib.kc_count.argtypes = [vp, vp, vp, u64, i32, i32, ctypes.POINTER(Result)]
+    lib.kc_count.restype = i32
+    lib.kc_free.argtypes = [vp, ctypes.POINTER(Result)]
+    lib.kc_free.restype = i32
+    lib.kc_result_copy_to_host.argtypes = [vp, ctypes.POINTER(Result), vp, vp]
+    lib.kc_result_copy_to_host.restype = i32
+    lib.kc_plan_destroy.argtypes = [vp]
+    lib.kc_plan_destroy.restype = i32
+    lib.kc_last_error.argtypes = []
+    lib.kc_last_error.restype = ctypes.c_char_p
+    lib.kc_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.kc_last_stats.restype = i32
+    lib.kc_last_kernel_times.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
+                                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)]
+    lib.kc_last_kernel_times.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(lib, st: int):
+    if st != KC_OK:
+        raise KcError(st, (lib.kc_last_error() or b"").decode())
+
+
+def _ptr(x):
+    """(pointer, keepalive) for a numpy array or torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x)
+        return x.ctypes.data, x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr(), x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class _DeviceArray:
+    """Exposes a device buffer through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+        self._owner = owner
+
+
+class CountResult:
+    """Device-resident sorted histogram; keys are uint64 [n] (k <= 32) or [n, 2] (lo, hi)."""
+
+    def __init__(self, counter: "KmerCounter", res: Result):
+        self._counter = counter
+        self._res = res
+
+    @property
+    def n(self) -> int:
+        return int(self._res.n)
+
+    @property
+    def key_words(self) -> int:
+        return int(self._res.key_words)
+
+    @property
+    def n_valid_windows(self) -> int:
+        return int(self._res.n_valid_windows)
+
+    def keys_tensor(self):
+        """Zero-copy int64 view of the key words (raw bits of the uint64 keys)."""
+        import torch
+        shape = (self.n,) if self.key_words == 1 else (self.n, 2)
+        return torch.as_tensor(_DeviceArray(self._res.keys or 0, shape, "<i8", self), device="cuda")
+
+    def counts_tensor(self):
+        """Zero-copy int32 view of the counts (raw bits of the uint32 counts)."""
+        import torch
+        return torch.as_tensor(_DeviceArray(self._res.counts or 0, (self.n,), "<i4", self), device="cuda")
+
+    def to_numpy(self):
+        lib = load_library()
+        keys = np.empty(self.n * self.key_words, dtype=np.uint64)
+        counts = np.empty(self.n, dtype=np.uint32)
+        _check(lib, lib.kc_result_copy_to_host(self._counter._plan, ctypes.byref(self._res),
+                                               keys.ctypes.data, counts.ctypes.data))
+        if self.key_words == 2:
+            keys = keys.reshape(self.n, 2)
+        return keys, counts
+
+    def free(self):
+        if self._res is not None and self._counter._plan:
+            lib = load_library()
+            _check(lib, lib.kc_free(self._counter._plan, ctypes.byref(self._res)))
+        self._res = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class KmerCounter:
+    """A plan (kc_plan) bound to one device and stream, with torch's caching allocator."""
+
+    def __init__(self, device: int | None = None, stream=None, use_torch_allocator: bool = True,
+                 n_partitions_hint: int = 0, table_load: float = 0.0, table_slots_max: int = 0,
+                 max_device_bytes: int = 0, profile: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("KmerCounter needs a CUDA device (no CPU fallback)")
+        lib = load_library()
+        self._lib = lib
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        opts = PlanOpts()
+        opts.device = self.device
+        opts.stream = ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream or 0))
+        if use_torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, strm, ctx):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, strm, ctx):
+                if ptr:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc_cb = _ALLOC_FN(_alloc)
+            self._free_cb = _FREE_FN(_free)
+            opts.alloc = self._alloc_cb
+            opts.free_ = self._free_cb
+        else:
+            opts.alloc = _ALLOC_FN()
+            opts.free_ = _FREE_FN()
+        opts.max_device_bytes = int(max_device_bytes)
+        opts.n_partitions_hint = int(n_partitions_hint)
+        opts.table_load = float(table_load)
+        opts.table_slots_max = int(table_slots_max)
+        opts.flags = KC_PLAN_PROFILE if profile else 0
+        plan = ctypes.c_void_p()
+        _check(lib, lib.kc_plan(ctypes.byref(opts), ctypes.byref(plan)))
+        self._opts = opts
+        self._plan = plan
+
+    def count(self, reads, offsets, k: int, canonical: bool = True) -> CountResult:
+        """Sorted (k-mer, count) histogram of the reads (host or device buffers)."""
+        rp, rk = _ptr(reads)
+        op, ok = _ptr(offsets)
+        n_reads = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+        if n_reads < 0:
+            raise ValueError("offsets must hold n_reads + 1 entries")
+        res = Result()
+        _check(self._lib, self._lib.kc_count(self._plan, rp, op, n_reads, int(k), int(bool(canonical)),
+                                             ctypes.byref(res)))
+        del rk, ok
+        return CountResult(self, res)
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._lib, self._lib.kc_last_stats(self._plan, ctypes.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in Stats._fields_}
+
+    def kernel_times(self) -> list[tuple[str, float]]:
+        """[(kernel name, device ms)] of the last count (plans created with profile=True)."""
+        n = ctypes.c_uint32()
+        names = (ctypes.c_char_p * 64)()
+        ms = (ctypes.c_float * 64)()
+        _check(self._lib, self._lib.kc_last_kernel_times(self._plan, 64, names, ms, ctypes.byref(n)))
+        return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, 64))]
+
+    def close(self):
+        if self._plan:
+            self._lib.kc_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

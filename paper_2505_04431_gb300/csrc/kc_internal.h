@@ -1,0 +1,108 @@
+// kc_internal.h - declarations shared by the kernels and the host orchestration.
+//
+// Data layout in device memory (one kc_count call):
+//   codes64[w]   bases 32w .. 32w+31 as 2-bit codes (A0 C1 G2 T3), first base in
+//                the two most significant bits (Algorithm 1's kmer << 2 order).
+//   inv32[w]     bit i set iff byte 32w+i is not one of ACGTacgt, or lies past
+//                the end of the input.
+//   hist[t][c]   phase-1 histogram: valid windows of tile t in coarse partition c.
+//   toff[t][c]   write offset of tile t inside partition c (bucket-major scan).
+//   kbuf         keys grouped by coarse partition (the owner partition of
+//                Algorithm 3's AsyncAdd, here a key range so that outputs concatenate
+//                in sorted order).
+//   sbuf         the same keys regrouped by fine partition inside each coarse one.
+//   out keys / counts   the sorted histogram.
+#pragma once
+#include <stdint.h>
+
+namespace kc {
+
+constexpr int kWordBases = 32;                 // bases per packed code word
+constexpr int kTileWords = 8192;               // one phase-1 tile = 262144 bases
+constexpr uint64_t kTileBases = (uint64_t)kTileWords * kWordBases;
+constexpr int kPackThreads = 512;              // pass A: one code word per thread per sub-step
+constexpr int kMaxCoarseLog2 = 12;             // at most 4096 coarse partitions
+constexpr int kMaxFineLog2 = 10;               // at most 1024 fine partitions per coarse one
+constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
+constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
+constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
+constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
+constexpr uint32_t kLookbackSpinLimit = 1u << 22;  // x ~100 ns sleep: ~0.4 s, then give up
+
+// status bits written by kernels (a kc_status is derived from them on the host)
+enum : uint32_t {
+  ST_COUNT_OVERFLOW = 1u,   // a count exceeded 2^32 - 1
+  ST_TIMEOUT = 2u,          // a bounded wait gave up
+  ST_BAD_OFFSETS = 4u,      // offsets not non-decreasing
+  ST_INTERNAL = 8u,         // an internal consistency check failed
+};
+
+// Values the host reads back at the end of a call.
+struct Meta {
+  uint64_t n_windows;   // K: valid windows
+  uint64_t n_distinct;  // D
+  uint64_t n_fine;      // number of fine partitions
+  uint64_t n_overflow;  // fine partitions that took the overflow path
+  uint32_t status;
+  uint32_t pad;
+  uint64_t ticket;      // phase-2 work counter
+};
+
+struct Shape {
+  uint64_t L;           // bases
+  uint64_t n_reads;
+  uint64_t n_words;     // ceil(L / 32)
+  uint64_t n_tiles;     // ceil(n_words / kTileWords)
+  int k;
+  int canonical;
+  int kw;               // key words: 1 or 2
+  int b1;               // log2 coarse partitions
+  int bT_max;           // log2 of the largest table
+  int tail;             // table slots past the home range (linear probing never wraps)
+  uint32_t fine_target; // keys per fine partition aimed for
+  uint64_t cap;         // capacity of kbuf / sbuf / outputs in keys
+  uint64_t nf_max;      // capacity of the fine-partition arrays
+  uint64_t smem_budget; // opt-in shared memory per block
+};
+
+struct Buffers {
+  const uint8_t* reads;
+  const uint64_t* offsets;
+  uint64_t* codes64;
+  uint32_t* inv32;
+  uint64_t* tile_first;   // first read index whose start is >= the tile's halo start
+  uint32_t* hist;         // [n_tiles][P1]
+  uint64_t* toff;         // [n_tiles][P1]
+  uint64_t* cstart;       // [P1 + 1] coarse partition starts
+  uint32_t* fine_base;    // [P1 + 1] first fine index of each coarse partition
+  uint8_t* fine_log2;     // [P1]
+  uint32_t* fhist;        // [nf_max] keys per fine partition
+  uint64_t* foff;         // [nf_max + 1] fine partition starts
+  unsigned long long* fcur;  // [nf_max] fine scatter cursors
+  unsigned long long* look;  // [nf_max] look-back status words
+  uint64_t* kbuf;
+  uint64_t* sbuf;
+  uint64_t* out_keys;
+  uint32_t* out_counts;
+  Meta* meta;
+};
+
+// Called after every kernel launch with the kernel's name (used for per-kernel timing).
+struct Marker {
+  void (*fn)(void* ctx, const char* name) = nullptr;
+  void* ctx = nullptr;
+  void operator()(const char* name) const {
+    if (fn) fn(ctx, name);
+  }
+};
+
+// Host launch wrappers (kc_kernels.cu).  Each returns the number of kernel launches, or
+// -cudaError_t if a launch failed (no later kernel is launched then).
+int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, const Marker& mark);
+int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, void* stream, const Marker& mark);
+int configure_kernels(int device);  // sets shared-memory attributes; returns 0 or a cudaError_t
+
+size_t count_kernel_smem(int kw, int bT_max, int tail);
+int table_log2_max(int kw, size_t smem_optin);
+
+}  // namespace kc

@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work: every comparison is bit-exact (keys and counts, byte for byte).
+Small and medium inputs are compared in full; the full-size workloads are checked
+on sampled keys that the oracle counts one by one (plus absent keys), and through
+properties that hold at any size (sum of counts = valid windows, strictly
+ascending keys, canonical keys not above their reverse complement)."""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.kmer_math import keys_as_ints, rc_key
+
+pytestmark = pytest.mark.gpu
+
+KS = [1, 2, 3, 4, 5, 8, 15, 16, 17, 31, 32, 33, 47, 63, 64]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def counter(torch_cuda):
+    from paper_2505_04431_gb300 import KmerCounter, build
+    build.build()
+    c = KmerCounter()
+    yield c
+    c.close()
+
+
+def gpu_count(counter, reads, offsets, k, canonical):
+    res = counter.count(reads, offsets, k, canonical)
+    try:
+        keys, counts = res.to_numpy()
+        return keys, counts, res.n_valid_windows
+    finally:
+        res.free()
+
+
+def assert_parity(counter, reads, offsets, k, canonical, tag=""):
+    ok, oc, onv = oracle.count(reads, offsets, k, canonical)
+    gk, gc, gnv = gpu_count(counter, reads, offsets, k, canonical)
+    assert gnv == onv, f"{tag} valid windows {gnv} != {onv}"
+    assert gk.shape == ok.shape, f"{tag} distinct {gk.shape} != {ok.shape}"
+    assert np.array_equal(gk, ok), f"{tag} keys differ"
+    assert np.array_equal(gc, oc), f"{tag} counts differ"
+
+
+def as_reads(strings):
+    bs = [s.encode() if isinstance(s, str) else s for s in strings]
+    offsets = np.zeros(len(bs) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([len(b) for b in bs])
+    reads = np.frombuffer(b"".join(bs), dtype=np.uint8).copy() if bs else np.zeros(0, np.uint8)
+    return reads, offsets
+
+
+# ---------------------------------------------------------------- small random inputs, every k
+@pytest.mark.parametrize("seed", range(4))
+def test_random_small_all_k(counter, seed):
+    rng = np.random.default_rng(100 + seed)
+    reads, offsets = synth.random_reads(rng, n_reads=int(rng.integers(1, 300)), max_len=200)
+    for k in KS:
+        for canonical in (False, True):
+            assert_parity(counter, reads, offsets, k, canonical, f"seed={seed} k={k} c={canonical}")
+
+
+def test_random_many_reads_cross_tiles(counter):
+    # ~1.3 M bases: several 262144-base tiles, reads straddle tile and word boundaries
+    rng = np.random.default_rng(7)
+    reads, offsets = synth.random_reads(rng, n_reads=9000, max_len=300, junk=0.001, n_rate=0.002)
+    for k in (21, 31, 32, 33, 63, 64):
+        assert_parity(counter, reads, offsets, k, True, f"k={k}")
+    assert_parity(counter, reads, offsets, 32, False, "k=32 fwd")
+    assert_parity(counter, reads, offsets, 64, False, "k=64 fwd")
+
+
+# ---------------------------------------------------------------- workload-shaped inputs
+@pytest.mark.parametrize("name,gen,seed,scale,k", [
+    ("uniform 1 Mbp 100 bp 10x", synth.UNIFORM_SHORT, 1001, 1.0, 31),
+    ("repeats 0.5 Mbp 150 bp 30x", synth.REPEAT_SHORT, 1002, 0.005, 31),
+    ("long noisy 1 Mbp 20x k63", synth.LONG_NOISY, 1003, 0.02, 63),
+])
+def test_workload_shapes(counter, name, gen, seed, scale, k):
+    reads, offsets, _ = synth.generate(gen, seed, scale)
+    assert_parity(counter, reads, offsets, k, True, name)
+
+
+def test_workload_shapes_forward_and_other_k(counter):
+    reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.3)
+    for k in (21, 31, 32):
+        assert_parity(counter, reads, offsets, k, False, f"fwd k={k}")
+    reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.005)
+    for k in (33, 47, 64):
+        assert_parity(counter, reads, offsets, k, True, f"long k={k}")
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_and_degenerate(counter):
+    for strings, k in [([], 31), ([""], 5), (["", "", ""], 1), (["ACG"], 4), (["N" * 500], 3),
+                       (["ACGT"], 4), (["ACGTN" * 40], 4), (["A" * 31], 31), (["a" * 64], 64)]:
+        r, o = as_reads(strings)
+        for canonical in (False, True):
+            assert_parity(counter, r, o, k, canonical, f"{strings[:1]} k={k}")
+
+
+def test_heavy_hitter_single_key(counter):
+    # 20000 identical homopolymer reads: one key with 2.42 M occurrences (all warp lanes equal)
+    r, o = as_reads(["A" * 150] * 20000)
+    ok, oc, _ = oracle.count(r, o, 31, True)
+    assert oc.tolist() == [20000 * 120]
+    assert_parity(counter, r, o, 31, True, "homopolymer")
+    assert_parity(counter, r, o, 63, True, "homopolymer k63")
+    # mixed: heavy key among random reads
+    rng = np.random.default_rng(3)
+    rr, ro = synth.random_reads(rng, n_reads=3000, max_len=150, junk=0.0, lower=0.0, n_rate=0.0)
+    strings = [bytes(rr[int(ro[i]):int(ro[i + 1])]) for i in range(3000)] + [b"AC" * 75] * 3000
+    r, o = as_reads(strings)
+    for k in (8, 31, 33):
+        assert_parity(counter, r, o, k, True, f"mixed heavy k={k}")
+
+
+def test_all_ones_key(counter):
+    # non-canonical k=32 / k=64: the all-T k-mer has every key bit set
+    for k in (32, 64):
+        r, o = as_reads(["T" * 100, "ACGT" * 30, "T" * k, "GGT" + "T" * 70])
+        assert_parity(counter, r, o, k, False, f"all-T k={k}")
+        assert_parity(counter, r, o, k, True, f"all-T canonical k={k}")
+
+
+def test_reads_exactly_k_and_tile_boundaries(counter):
+    # reads of exactly k bases; read starts placed at and next to the 262144-base tile boundary
+    rng = np.random.default_rng(5)
+    seqs = []
+    total = 0
+    while total < 262144 - 40:
+        n = int(rng.integers(1, 200))
+        seqs.append("".join("ACGT"[i] for i in rng.integers(0, 4, n)))
+        total += n
+    seqs.append("C" * (262144 - total))  # next read starts exactly at the boundary
+    seqs += ["".join("ACGT"[i] for i in rng.integers(0, 4, 31)) for _ in range(3000)]
+    r, o = as_reads(seqs)
+    assert int(o[len(seqs) - 3000]) == 262144
+    assert_parity(counter, r, o, 31, True, "exact-k reads")
+    assert_parity(counter, r, o, 5, False, "exact-k reads k5")
+
+
+def test_overflow_path_forced(torch_cuda):
+    # tiny tables: nearly every fine partition overflows and is split by key range
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(table_slots_max=64)
+    try:
+        reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.05)
+        assert_parity(c, reads, offsets, 31, True, "forced overflow k31")
+        assert c.stats()["n_overflow_fine"] > 0
+        reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.002)
+        assert_parity(c, reads, offsets, 63, True, "forced overflow k63")
+        r, o = as_reads(["T" * 100, "ACGT" * 30, "T" * 32, "GATTACA" * 20])
+        assert_parity(c, r, o, 32, False, "forced overflow all-T")
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("hint", [1, 4096])
+def test_partition_count_extremes(torch_cuda, hint):
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(n_partitions_hint=hint)
+    try:
+        reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.2)
+        assert_parity(c, reads, offsets, 31, True, f"P1={hint}")
+        reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.002)
+        assert_parity(c, reads, offsets, 63, True, f"P1={hint} k63")
+    finally:
+        c.close()
+
+
+def test_input_memory_kinds(counter, torch_cuda):
+    torch = torch_cuda
+    reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.05)
+    ok, oc, onv = oracle.count(reads, offsets, 31, True)
+
+    def check(r, o, tag):
+        gk, gc, gnv = gpu_count(counter, r, o, 31, True)
+        assert gnv == onv and np.array_equal(gk, ok) and np.array_equal(gc, oc), tag
+
+    rt, ot = torch.from_numpy(reads), torch.from_numpy(offsets.astype(np.int64))
+    check(reads, offsets, "numpy host")
+    check(rt.pin_memory(), ot.pin_memory(), "pinned host")
+    check(rt.cuda(), ot.cuda(), "device")
+    # device reads at an address that is not 16-byte aligned
+    buf = torch.empty(len(reads) + 1, dtype=torch.uint8, device="cuda")
+    buf[1:] = rt.cuda()
+    check(buf[1:], ot.cuda(), "unaligned device")
+    # host offsets, device reads
+    check(rt.cuda(), offsets, "mixed")
+
+
+def test_bad_offsets_rejected(counter, torch_cuda):
+    from paper_2505_04431_gb300 import KC_EINVAL, KcError
+    reads = np.frombuffer(b"ACGTACGTAC", dtype=np.uint8).copy()
+    bad = np.array([0, 6, 3, 10], dtype=np.uint64)
+    with pytest.raises(KcError) as e:
+        counter.count(reads, bad, 3, True)
+    assert e.value.status == KC_EINVAL
+    torch = torch_cuda
+    with pytest.raises(KcError) as e:
+        counter.count(torch.from_numpy(reads).cuda(), torch.from_numpy(bad.astype(np.int64)).cuda(), 3, True)
+    assert e.value.status == KC_EINVAL
+    with pytest.raises(KcError):
+        counter.count(reads, np.array([1, 10], dtype=np.uint64), 3, True)
+    for k in (0, 65):
+        with pytest.raises(KcError):
+            counter.count(reads, np.array([0, 10], dtype=np.uint64), k, True)
+    # the plan still works afterwards
+    assert_parity(counter, reads, np.array([0, 4, 10], dtype=np.uint64), 3, True, "after errors")
+
+
+def test_repeated_calls_identical(counter):
+    reads, offsets, _ = synth.generate(synth.REPEAT_SHORT, 1002, 0.002)
+    a = gpu_count(counter, reads, offsets, 31, True)
+    b = gpu_count(counter, reads, offsets, 31, True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------- full-size, sampled
+def _oracle_parallel_counts(reads, offsets, k, canonical, query, n_chunks):
+    """oracle.count_keys over read ranges in threads (the C call releases the GIL);
+    counts add up across disjoint read sets (additivity is pinned in test_oracle)."""
+    n = len(offsets) - 1
+    cuts = np.linspace(0, n, n_chunks + 1).astype(np.int64)
+
+    def part(i):
+        a, b = int(cuts[i]), int(cuts[i + 1])
+        o = offsets[a:b + 1] - offsets[a]
+        r = reads[int(offsets[a]):int(offsets[b])]
+        return oracle.count_keys(r, o, k, canonical, query), oracle.valid_windows(r, o, k)
+
+    with cf.ThreadPoolExecutor(n_chunks) as ex:
+        parts = list(ex.map(part, range(n_chunks)))
+    return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+
+@pytest.mark.parametrize("name", ["repeats_100mbp_150bp_30x_k31", "long_50mbp_10kbp_20x_k63"])
+def test_full_size_sampled(counter, torch_cuda, name):
+    torch = torch_cuda
+    reads, offsets, k = synth.workload(name)
+    rt = torch.from_numpy(reads).cuda()
+    ot = torch.from_numpy(offsets.view(np.int64)).cuda()
+    res = counter.count(rt, ot, k, True)
+    try:
+        n = res.n
+        keys_t = res.keys_tensor()          # int64 view of the key bits
+        counts_t = res.counts_tensor().to(torch.int64) & 0xFFFFFFFF
+        kw = res.key_words
+        # properties that hold at any size, checked on the device
+        kv = keys_t
+        if kw == 1:
+            hi, lo = None, kv
+        else:
+            lo, hi = kv[:, 0], kv[:, 1]
+        # strictly ascending as unsigned: compare with the sign bit flipped
+        flip = torch.tensor(-(2**63), dtype=torch.int64, device="cuda")
+        if kw == 1:
+            a = lo ^ flip
+            assert bool((a[1:] > a[:-1]).all())
+        else:
+            ah, al = hi ^ flip, lo ^ flip
+            gt = (ah[1:] > ah[:-1]) | ((ah[1:] == ah[:-1]) & (al[1:] > al[:-1]))
+            assert bool(gt.all())
+        total = int(counts_t.sum().item())
+        assert bool((counts_t >= 1).all())
+        # sampled keys, counted one by one by the oracle, plus keys that must be absent
+        rng = np.random.default_rng(9)
+        idx = np.unique(rng.integers(0, n, size=1500))
+        idx_t = torch.from_numpy(idx).cuda()
+        sk = keys_t[idx_t].cpu().numpy().view(np.uint64)
+        sc = counts_t[idx_t].cpu().numpy().astype(np.uint64)
+        ints = keys_as_ints(sk)
+        for v in ints[:200]:
+            assert v <= rc_key(v, k)
+        # absent: key + 1 where the next output key is not key + 1
+        nxt = keys_t[torch.clamp(idx_t + 1, max=n - 1)].cpu().numpy().view(np.uint64)
+        nxt_ints = keys_as_ints(nxt)
+        absent = sorted({v + 1 for v, w in zip(ints, nxt_ints) if w != v + 1 and v + 1 < 4**k and v + 1 != w})
+        absent = [a for a in absent if a not in set(ints)][:300]
+        query_ints = sorted(set(ints) | set(absent))
+        if kw == 1:
+            q = np.array(query_ints, dtype=np.uint64)
+        else:
+            q = np.array([[v & (2**64 - 1), v >> 64] for v in query_ints], dtype=np.uint64)
+        ocounts, onv = _oracle_parallel_counts(reads, offsets, k, True, q, min(16, os.cpu_count() or 4))
+        expect = dict(zip(query_ints, [int(x) for x in ocounts]))
+        for v, c in zip(ints, sc):
+            assert expect[v] == int(c), f"key {v}: gpu {int(c)} oracle {expect[v]}"
+        for a in absent:
+            assert expect[a] == 0, f"absent key {a} occurs {expect[a]} times"
+        assert total == onv == res.n_valid_windows
+    finally:
+        res.free()
