@@ -196,7 +196,7 @@ def run_ours(args):
         kcbuild.build()
     if dist:
         dist.barrier()
-    reads, offsets, k = synth.workload(args.workload)
+    reads, offsets, k = synth.workload(args.workload, args.scale)
     n_reads, L = len(offsets) - 1, len(reads)
     stream = torch.cuda.Stream(dev)
     counter = KmerCounter(device=dev, stream=stream, profile=True)
@@ -304,6 +304,7 @@ def run_ours(args):
                           "frac": B / (ms_per_step / 1e3) / 1e9 / peak},
         "kernels_ms": {n: round(v, 4) for n, v in sorted(avg.items(), key=lambda x: -x[1])},
         "gpu_launches": launches,
+        "stats": counter.stats(),
         "clocks": clk,
         "e2e": e2e,
         "wall_s": wall,
@@ -325,6 +326,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="genome scale (diagnostics only; 1.0 = the workload)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

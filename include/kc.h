@@ -121,6 +121,9 @@ typedef struct {
   uint64_t n_fine;             /* fine partitions (one shared-memory table each) */
   uint64_t n_overflow_fine;    /* fine partitions that needed the overflow path */
   uint64_t workspace_bytes;    /* scratch currently held by the plan */
+  uint64_t phase_cycles[8];    /* KC_PLAN_PROFILE only: SM cycles of the count kernel's phases
+                                  (clear, insert, sort, count, look-back, emit, overflow path,
+                                  setup), summed over its thread blocks */
 } kc_stats;
 kc_status kc_last_stats(kc_plan_t plan, kc_stats *out);
 

@@ -285,6 +285,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   const uint32_t nf_max = (uint32_t)nf_max64;
   s.nf_max = nf_max;
   s.smem_budget = p->smem_optin;
+  s.profile = p->profile ? 1 : 0;
 
   // ---- scratch layout
   Layout lay;
@@ -398,6 +399,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   p->stats.n_partitions = (uint32_t)P1;
   p->stats.n_fine = m.n_fine;
   p->stats.n_overflow_fine = m.n_overflow;
+  for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
   if (m.status & kc::ST_BAD_OFFSETS) return bail(KC_EINVAL, "kc_count: offsets must start at 0 and be non-decreasing");
   if (m.status & kc::ST_COUNT_OVERFLOW) return bail(KC_EOVERFLOW, "kc_count: a count exceeds 2^32 - 1");
   if (m.status & kc::ST_TIMEOUT) return bail(KC_ETIMEOUT, "kc_count: a device-side wait timed out");

@@ -46,6 +46,7 @@ struct Meta {
   uint32_t status;
   uint32_t pad;
   uint64_t ticket;      // phase-2 work counter
+  uint64_t phase_cycles[8];  // profiled plans only: SM cycles per phase of k_count_emit, summed over CTAs
 };
 
 struct Shape {
@@ -63,6 +64,7 @@ struct Shape {
   uint64_t cap;         // capacity of kbuf / sbuf / outputs in keys
   uint64_t nf_max;      // capacity of the fine-partition arrays
   uint64_t smem_budget; // opt-in shared memory per block
+  int profile;          // nonzero: k_count_emit accumulates per-phase cycle counts
 };
 
 struct Buffers {

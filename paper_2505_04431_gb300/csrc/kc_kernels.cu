@@ -771,34 +771,46 @@ struct Table {
   uint32_t* counts;
 };
 
-size_t count_kernel_smem(int kw, int bT_max, int tail) {
-  const size_t slots = ((size_t)1 << bT_max) + (size_t)tail;
+// Count kernel shared memory: a hash table of 2^bT_max slots (key + count).  After the
+// count, the same bytes hold the dense array of distinct keys (at most 3/4 of the slots)
+// and the bucket histogram used to order them.
+size_t count_kernel_smem(int kw, int bT_max, int /*unused*/) {
+  const size_t slots = (size_t)1 << bT_max;
   return slots * (size_t)(kw * 8 + 4) + 256;
 }
 
 int table_log2_max(int kw, size_t smem_optin) {
   int best = 6;
-  for (int bt = 6; bt <= 16; ++bt) {
-    const int tail = bt >= 10 ? 1024 : (1 << bt);
-    if (count_kernel_smem(kw, bt, tail) + 8192 <= smem_optin) best = bt;  // 8 KB for static shared memory
-  }
+  for (int bt = 6; bt <= 16; ++bt)
+    if (count_kernel_smem(kw, bt, 0) + 8192 <= smem_optin) best = bt;  // 8 KB for static shared memory
   return best;
 }
 
-struct CountCtx {
-  int k, canonical, b1;
-};
+constexpr int kProbeLimit = 128;
+constexpr int kWorkers = kCountThreads - 32;  // warps 1.. order and sort while warp 0 looks back
+constexpr int kBigCap = 256;                  // buckets too large for one thread, sorted per warp
 
-// Insert `inc` occurrences of `key`, home slot h; returns false if no slot is found
-// within the probe limit (the caller then takes the overflow path).
+// counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes)
+__device__ __forceinline__ uint32_t hslot(uint64_t key, int bT) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bT));
+}
+__device__ __forceinline__ uint32_t hslot(u128 key, int bT) {
+  const uint64_t h = ((uint64_t)key ^ ((uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
+  return (uint32_t)(h >> (64 - bT));
+}
+
+__device__ __forceinline__ void bar_workers() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory"); }
+
+// Add `inc` to the count of `key` (claiming a slot if new).  Returns false if no slot
+// was found within the probe limit.
 template <int KW>
-__device__ __forceinline__ bool table_insert(Table<KW> tb, typename KeyT<KW>::T key, uint32_t inc, uint32_t h,
-                                             uint32_t nslots, uint32_t* status) {
+__device__ __forceinline__ bool count_insert(Table<KW> tb, typename KeyT<KW>::T key, uint32_t inc, int bT,
+                                             uint32_t* n_new, uint32_t* status) {
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
-  uint32_t s = h;
-  for (int probe = 0; probe < 512; ++probe, ++s) {
-    if (s >= nslots) return false;
+  const uint32_t mask = (1u << bT) - 1;
+  uint32_t s = hslot(key, bT);
+  for (int probe = 0; probe < kProbeLimit; ++probe, s = (s + 1) & mask) {
     bool hit = false;
     if constexpr (KW == 1) {
       uint64_t* p = reinterpret_cast<uint64_t*>(tb.keys) + s;
@@ -807,10 +819,12 @@ __device__ __forceinline__ bool table_insert(Table<KW> tb, typename KeyT<KW>::T 
         hit = true;
       } else if (cur == ~0ull) {
         const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(p), ~0ull, (unsigned long long)key);
+        if (old == ~0ull) atomicAdd(n_new, 1u);
         hit = (old == ~0ull || old == (unsigned long long)key);
       }
     } else {
       const K old = cas128_shared(reinterpret_cast<u128*>(tb.keys) + s, (u128)EMPTY, (u128)key);
+      if (old == EMPTY) atomicAdd(n_new, 1u);
       hit = (old == EMPTY || old == key);
     }
     if (hit) {
@@ -822,84 +836,6 @@ __device__ __forceinline__ bool table_insert(Table<KW> tb, typename KeyT<KW>::T 
   return false;
 }
 
-// Sort the keys inside every run of occupied slots (collisions leave them unordered);
-// runs are disjoint, each is owned by the thread whose slice holds its first slot.
-template <int KW>
-__device__ void sort_clusters(Table<KW> tb, uint32_t nslots) {
-  typedef typename KeyT<KW>::T K;
-  const K EMPTY = all_ones<K>();
-  const uint32_t per = (nslots + blockDim.x - 1) / blockDim.x;
-  const uint32_t lo = min(nslots, threadIdx.x * per), hi = min(nslots, lo + per);
-  for (uint32_t s = lo; s < hi; ++s) {
-    if (tb.keys[s] == EMPTY || (s > 0 && tb.keys[s - 1] != EMPTY)) continue;
-    uint32_t e = s + 1;
-    while (e < nslots && tb.keys[e] != EMPTY) ++e;
-    for (uint32_t i = s + 1; i < e; ++i) {  // insertion sort of [s, e)
-      const K kv = tb.keys[i];
-      const uint32_t cv = tb.counts[i];
-      uint32_t m = i;
-      while (m > s && tb.keys[m - 1] > kv) {
-        tb.keys[m] = tb.keys[m - 1];
-        tb.counts[m] = tb.counts[m - 1];
-        --m;
-      }
-      tb.keys[m] = kv;
-      tb.counts[m] = cv;
-    }
-  }
-}
-
-// Count occupied slots (warp-contiguous slices), then write them in slot order at
-// out + base.  Returns the number written.  All threads call it; `wcnt` has 33 entries.
-template <int KW>
-__device__ uint64_t emit_table(Table<KW> tb, uint32_t nslots, bool write, uint64_t base, uint64_t* out_keys,
-                               uint32_t* out_counts, uint32_t* wcnt, uint64_t cap, uint32_t* status) {
-  typedef typename KeyT<KW>::T K;
-  const K EMPTY = all_ones<K>();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t chunks = (nslots + 31) / 32;
-  const uint32_t per = (chunks + nw - 1) / nw;
-  const uint32_t c_lo = min(chunks, wid * per), c_hi = min(chunks, c_lo + per);
-  uint32_t cnt = 0;
-  for (uint32_t ch = c_lo; ch < c_hi; ++ch) {
-    const uint32_t s = ch * 32 + lane;
-    cnt += __popc(__ballot_sync(0xffffffffu, s < nslots && tb.keys[s] != EMPTY));
-  }
-  if (lane == 0) wcnt[wid] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int w = 0; w < nw; ++w) {
-      const uint32_t v = wcnt[w];
-      wcnt[w] = run;
-      run += v;
-    }
-    wcnt[32] = run;
-  }
-  __syncthreads();
-  const uint64_t total = wcnt[32];
-  if (write) {
-    uint64_t pos = base + wcnt[wid];
-    for (uint32_t ch = c_lo; ch < c_hi; ++ch) {
-      const uint32_t s = ch * 32 + lane;
-      const bool occ = s < nslots && tb.keys[s] != EMPTY;
-      const unsigned m = __ballot_sync(0xffffffffu, occ);
-      if (occ) {
-        const uint64_t o = pos + __popc(m & ((1u << lane) - 1));
-        if (o < cap) {
-          store_key(out_keys, o, tb.keys[s]);
-          out_counts[o] = tb.counts[s];
-        } else {
-          atomicOr(status, ST_INTERNAL);
-        }
-      }
-      pos += __popc(m);
-    }
-  }
-  __syncthreads();
-  return total;
-}
-
 template <int KW>
 __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
   typedef typename KeyT<KW>::T K;
@@ -909,42 +845,229 @@ __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
   }
 }
 
-// Insert the keys in[0, n) whose value lies in [lo, hi] (all of them when `ranged` is
-// false) with home slot h(key).  Sets *ovf if some key found no slot.
-template <int KW, class H>
-__device__ void insert_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
-                           typename KeyT<KW>::T hi, uint32_t nslots, H&& home, uint32_t* ovf, uint32_t* special,
-                           uint32_t* status) {
+// Count the keys in[0, n) (only those in [lo, hi] when `ranged`).  The all-ones key is
+// counted apart in *special (it marks empty slots).  Sets *ovf if a key found no slot.
+template <int KW>
+__device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
+                          typename KeyT<KW>::T hi, int bT, uint32_t* n_new, uint32_t* ovf, uint32_t* special,
+                          uint32_t* status) {
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
   const int lane = threadIdx.x & 31;
-  for (uint64_t base = 0; base < n; base += blockDim.x) {
-    const uint64_t i = base + threadIdx.x;
-    K key = 0;
-    bool act = i < n;
-    if (act) load_key(in, i, key);
-    if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
-    const unsigned am = __ballot_sync(0xffffffffu, act);
-    if (!am) continue;
-    const int first = __ffs(am) - 1;
-    const K k0 = shfl_key(key, first);
-    const bool same = __all_sync(0xffffffffu, !act || key == k0);
-    if (same) {
-      if (lane == first) {
-        const uint32_t inc = __popc(am);
-        if (k0 == EMPTY) {
-          if (atomicAdd(special, inc) > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
-        } else if (!table_insert<KW>(tb, k0, inc, home(k0), nslots, status)) {
+  for (uint64_t base = 0; base < n; base += 2 * (uint64_t)blockDim.x) {
+    K kk[2];
+    bool aa[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {  // two loads in flight per thread
+      const uint64_t i = base + (uint64_t)m * blockDim.x + threadIdx.x;
+      kk[m] = 0;
+      aa[m] = i < n;
+      if (aa[m]) load_key(in, i, kk[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const K key = kk[m];
+      bool act = aa[m];
+      if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
+      const unsigned am = __ballot_sync(0xffffffffu, act);
+      if (!am) continue;
+      const int first = __ffs(am) - 1;
+      const K k0 = shfl_key(key, first);
+      const bool same = __all_sync(0xffffffffu, !act || key == k0);
+      if (same) {  // a warp of equal keys (heavy hitter) adds once
+        if (lane == first) {
+          const uint32_t inc = __popc(am);
+          if (k0 == EMPTY) {
+            if (atomicAdd(special, inc) > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
+          } else if (!count_insert<KW>(tb, k0, inc, bT, n_new, status)) {
+            atomicOr(ovf, 1u);
+          }
+        }
+      } else if (act) {
+        if (key == EMPTY) {
+          if (atomicAdd(special, 1u) == 0xffffffffu) atomicOr(status, ST_COUNT_OVERFLOW);
+        } else if (!count_insert<KW>(tb, key, 1u, bT, n_new, status)) {
           atomicOr(ovf, 1u);
         }
       }
-    } else if (act) {
-      if (key == EMPTY) {
-        if (atomicAdd(special, 1u) == 0xffffffffu) atomicOr(status, ST_COUNT_OVERFLOW);
-      } else if (!table_insert<KW>(tb, key, 1u, home(key), nslots, status)) {
-        atomicOr(ovf, 1u);
+    }
+  }
+}
+
+// Write the occupied slots (unordered) to stage_keys / stage_counts[0, d).
+template <int KW>
+__device__ void stage_table(Table<KW> tb, uint32_t nslots, uint64_t* stage_keys, uint32_t* stage_counts,
+                            uint32_t* cursor) {
+  typedef typename KeyT<KW>::T K;
+  const K EMPTY = all_ones<K>();
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = (threadIdx.x & ~31u); base < nslots; base += blockDim.x) {
+    const uint32_t s = base + lane;
+    const bool occ = s < nslots && tb.keys[s] != EMPTY;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    uint32_t pos = 0;
+    if (lane == 0 && m) pos = atomicAdd(cursor, __popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (occ) {
+      const uint32_t o = pos + __popc(m & ((1u << lane) - 1));
+      store_key(stage_keys, o, tb.keys[s]);
+      stage_counts[o] = tb.counts[s];
+    }
+  }
+}
+
+// Exclusive scan of data[0, n) by the worker threads (named barrier 1); returns the total.
+template <typename T>
+__device__ T workers_exclusive_scan(T* data, int n, T* warp_tmp) {
+  const int t = threadIdx.x - 32, nt = kWorkers, lane = t & 31, wid = t >> 5, nw = kWorkers / 32;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  T s = 0;
+  for (int i = lo; i < hi; ++i) s += data[i];
+  T x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  bar_workers();
+  if (wid == 0) {
+    T w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_tmp[lane] = w;
+  }
+  bar_workers();
+  T run = x - s + (wid ? warp_tmp[wid - 1] : 0);
+  const T total = warp_tmp[nw - 1];
+  for (int i = lo; i < hi; ++i) {
+    T v = data[i];
+    data[i] = run;
+    run += v;
+  }
+  bar_workers();
+  return total;
+}
+
+// Sort keys[a, a+c) (with their counts) by one warp: a bitonic network whose comparators
+// all put the smaller key first, so positions past c act as +infinity and are skipped.
+template <class K>
+__device__ void warp_sort_segment(K* keys, uint32_t* counts, uint32_t a, uint32_t c) {
+  const int lane = threadIdx.x & 31;
+  uint32_t M = 1;
+  while (M < c) M <<= 1;
+  for (uint32_t size = 2; size <= M; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = lane; i < M; i += 32) {
+        const uint32_t j = (stride == (size >> 1)) ? (i ^ (size - 1)) : (i ^ stride);
+        if (j > i && j < c) {
+          const K x = keys[a + i], y = keys[a + j];
+          if (y < x) {
+            keys[a + i] = y;
+            keys[a + j] = x;
+            const uint32_t cx = counts[a + i];
+            counts[a + i] = counts[a + j];
+            counts[a + j] = cx;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Order the d staged entries by key into dense_keys / dense_counts (shared memory):
+// an ordered counting sort into NB buckets (bucket = bfn(key), non-decreasing in the
+// key), then a sort inside every bucket.  Run by the worker warps only.
+template <int KW, class B>
+__device__ void order_entries(const uint64_t* stage_keys, const uint32_t* stage_counts, uint32_t d,
+                              typename KeyT<KW>::T* dense_keys, uint32_t* dense_counts, uint32_t* hist, uint32_t NB,
+                              B&& bfn, uint32_t* big_list, uint32_t* big_n, uint32_t* warp_tmp) {
+  typedef typename KeyT<KW>::T K;
+  const int t = threadIdx.x - 32;
+  for (uint32_t i = t; i < NB; i += kWorkers) hist[i] = 0;
+  if (t == 0) *big_n = 0;
+  bar_workers();
+  constexpr int kMaxPer = 16;  // d <= kMaxPer * kWorkers (checked by the caller)
+  uint32_t br[kMaxPer];
+#pragma unroll
+  for (int m = 0; m < kMaxPer; ++m) {
+    const uint32_t i = t + m * kWorkers;
+    br[m] = 0xffffffffu;
+    if (i < d) {
+      K key;
+      load_key(stage_keys, i, key);
+      const uint32_t bk = bfn(key);
+      const uint32_t r = atomicAdd(&hist[bk], 1u);
+      br[m] = (bk << 16) | r;  // NB <= 2^15 buckets, rank < 2^16
+    }
+  }
+  bar_workers();
+  // bucket sizes are kept in the second half of hist's space? no: scan in place, sizes recomputed below
+  workers_exclusive_scan<uint32_t>(hist, (int)NB, warp_tmp);
+#pragma unroll
+  for (int m = 0; m < kMaxPer; ++m) {
+    const uint32_t i = t + m * kWorkers;
+    if (i < d) {
+      K key;
+      load_key(stage_keys, i, key);
+      const uint32_t pos = hist[br[m] >> 16] + (br[m] & 0xffffu);
+      dense_keys[pos] = key;
+      dense_counts[pos] = stage_counts[i];
+    }
+  }
+  bar_workers();
+  // sort inside buckets: short ones by one thread, long ones queued for a warp
+  for (uint32_t bk = t; bk < NB; bk += kWorkers) {
+    const uint32_t a = hist[bk];
+    const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
+    const uint32_t c = e - a;
+    if (c < 2) continue;
+    if (c > 32) {
+      const uint32_t q = atomicAdd(big_n, 1u);
+      if (q < kBigCap) {
+        big_list[q] = bk;
+        continue;
       }
     }
+    for (uint32_t i = a + 1; i < e; ++i) {
+      const K kv = dense_keys[i];
+      const uint32_t cv = dense_counts[i];
+      uint32_t m = i;
+      while (m > a && dense_keys[m - 1] > kv) {
+        dense_keys[m] = dense_keys[m - 1];
+        dense_counts[m] = dense_counts[m - 1];
+        --m;
+      }
+      dense_keys[m] = kv;
+      dense_counts[m] = cv;
+    }
+  }
+  bar_workers();
+  const uint32_t nbig = min(*big_n, (uint32_t)kBigCap);
+  for (uint32_t q = (uint32_t)(t >> 5); q < nbig; q += kWorkers / 32) {
+    const uint32_t bk = big_list[q];
+    const uint32_t a = hist[bk];
+    const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
+    warp_sort_segment<K>(dense_keys, dense_counts, a, e - a);
+  }
+}
+
+// Coalesced copy of the dense sorted entries to out[base, base + d).
+template <int KW>
+__device__ void emit_dense(const typename KeyT<KW>::T* dense_keys, const uint32_t* dense_counts, uint32_t d,
+                           uint64_t base, uint64_t* out_keys, uint32_t* out_counts, uint64_t cap, uint32_t* status) {
+  if (base + d > cap) {
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    return;
+  }
+  for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+    store_key(out_keys, base + i, dense_keys[i]);
+    out_counts[base + i] = dense_counts[i];
   }
 }
 
@@ -955,17 +1078,17 @@ template <> __device__ __forceinline__ int bitlen(u128 v) {
   return hi ? 128 - __clzll(hi) : 64 - __clzll((uint64_t)v);
 }
 
+__device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
+
 template <int KW>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
-  const uint32_t cap = (1u << s.bT_max) + (uint32_t)s.tail;
-  Table<KW> tb;
-  tb.keys = reinterpret_cast<K*>(sm);
-  tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap);
+  const uint32_t cap_slots = 1u << s.bT_max;
   __shared__ uint64_t g_s, excl_s;
-  __shared__ uint32_t ovf_s, special_s, nfine_c_s, c_s;
-  __shared__ uint32_t wcnt[33];
+  __shared__ uint32_t ovf_s, special_s, nnew_s, cursor_s, c_s, flog_s, big_n;
+  __shared__ uint32_t wtmp[32];
+  __shared__ uint32_t big_list[kBigCap];
   __shared__ K red_lo[32], red_hi[32];
   __shared__ K stk_lo[160], stk_hi[160];
   __shared__ int stk_n;
@@ -973,11 +1096,31 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
   const int P1 = 1 << s.b1;
   const uint64_t NF = b.meta->n_fine;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* stage_cnt_all = reinterpret_cast<uint32_t*>(b.kbuf);  // kbuf is free once the fine split is done
+  // profiled plans: thread 0 adds the cycles spent in each phase (0 clear, 1 count, 2 stage,
+  // 3 order + sort, 4 look-back, 5 emit, 6 overflow path, 7 ticket + setup)
+  long long t_mark = clock64();
+  auto phase = [&](int i) {
+    if (s.profile && threadIdx.x == 0) {
+      const long long now = clock64();
+      atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[i]), (unsigned long long)(now - t_mark));
+      t_mark = now;
+    }
+  };
+  // the dense array and histogram reuse the table bytes: layout for a table of 2^bT slots
+  auto dense_layout = [&](int bT, K*& dk, uint32_t*& dc, uint32_t*& hist, uint32_t& dcap) {
+    dcap = (3u << bT) >> 2;
+    dk = reinterpret_cast<K*>(sm);
+    dc = reinterpret_cast<uint32_t*>(dk + dcap);
+    hist = dc + dcap;
+  };
   while (true) {
     if (threadIdx.x == 0) {
       g_s = atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->ticket), 1ull);
       ovf_s = 0;
       special_s = 0;
+      nnew_s = 0;
+      cursor_s = 0;
     }
     __syncthreads();
     const uint64_t g = g_s;
@@ -996,58 +1139,74 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         if (b.fine_base[mid] <= (uint32_t)g) lo = mid; else hi = mid - 1;
       }
       c_s = (uint32_t)lo;
-      nfine_c_s = b.fine_log2[lo];
+      flog_s = b.fine_log2[lo];
     }
-    // table size: at least twice the keys (all distinct at most), within the cap
+    // table: at least twice the keys (at most that many distinct), within the cap
     int bT = 6;
     while (bT < s.bT_max && ((uint64_t)1 << bT) < 2 * n) ++bT;
-    const uint32_t tail = min((uint32_t)s.tail, 1u << bT);
-    const uint32_t nslots = (1u << bT) + tail;
-    table_clear<KW>(tb, nslots);
+    Table<KW> tb;
+    tb.keys = reinterpret_cast<K*>(sm);
+    tb.counts = reinterpret_cast<uint32_t*>(tb.keys + (1u << bT));
+    phase(7);
+    table_clear<KW>(tb, 1u << bT);
     __syncthreads();
-    const int skip = s.b1 + (int)nfine_c_s;
-    const int kk = s.k, canon = s.canonical;
-    insert_all<KW>(tb, in, n, false, K(0), K(0), nslots,
-                   [&](K key) { return field(utrans(top64(key, kk), canon), skip, bT); }, &ovf_s, &special_s,
-                   &b.meta->status);
+    phase(0);
+    count_all<KW>(tb, in, n, false, K(0), K(0), bT, &nnew_s, &ovf_s, &special_s, &b.meta->status);
     __syncthreads();
-    if (!ovf_s) {
-      sort_clusters<KW>(tb, nslots);
+    phase(1);
+    K* dk;
+    uint32_t *dc, *hist, dcap;
+    dense_layout(bT, dk, dc, hist, dcap);
+    const uint32_t dn = nnew_s;
+    if (!ovf_s && dn <= dcap && dn <= 16u * kWorkers) {
+      const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
+      if (threadIdx.x == 0) st_release(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
+      // stage the distinct entries in this partition's spent input region
+      stage_table<KW>(tb, 1u << bT, b.sbuf + f0 * KW, stage_cnt_all + f0, &cursor_s);
       __syncthreads();
-      const uint64_t d = emit_table<KW>(tb, nslots, false, 0, nullptr, nullptr, wcnt, 0, nullptr) + (special_s ? 1 : 0);
+      phase(2);
       if (wid == 0) {
-        if (lane == 0) st_release(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
         const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
         if (lane == 0) {
           if (g > 0) st_release(&b.look[g], kLookIncl | (ex + d));
           excl_s = ex;
         }
+      } else {
+        uint32_t NB = 1;
+        while (NB < 32768u && NB * 2 <= dn) NB <<= 1;  // about two entries per bucket
+        const int bB = ceil_log2_u32(NB);
+        const int skip = s.b1 + (int)flog_s;
+        const int kk = s.k, canon = s.canonical;
+        order_entries<KW>(b.sbuf + f0 * KW, stage_cnt_all + f0, dn, dk, dc, hist, NB,
+                          [&](K key) { return field(utrans(top64(key, kk), canon), skip, bB); }, big_list, &big_n,
+                          wtmp);
       }
       __syncthreads();
+      phase(3);
       const uint64_t ex = excl_s;
-      const uint64_t wrote = emit_table<KW>(tb, nslots, true, ex, b.out_keys, b.out_counts, wcnt, s.cap, &b.meta->status);
+      emit_dense<KW>(dk, dc, dn, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       if (special_s && threadIdx.x == 0) {
-        if (ex + wrote < s.cap) {
-          store_key(b.out_keys, ex + wrote, EMPTY);
-          b.out_counts[ex + wrote] = special_s;
+        if (ex + dn < s.cap) {
+          store_key(b.out_keys, ex + dn, EMPTY);
+          b.out_counts[ex + dn] = special_s;
         } else {
           atomicOr(&b.meta->status, ST_INTERNAL);
         }
       }
       __syncthreads();
+      phase(5);
       continue;
     }
-    // ---------------- overflow path: too many distinct keys, or a long collision run.
-    // Split the partition's key range into sub-ranges, each counted in its own table
-    // with home slot (key - lo) >> shift; a sub-range narrower than the table has no
-    // collisions at all, so the splitting ends.  The exclusive prefix is resolved first
-    // because the partial outputs are written before the total is known.
+    // ---------------- overflow path: too many distinct keys for the table.  Split the
+    // partition's key range into sub-ranges, each counted in its own table and ordered
+    // with buckets (key - lo) >> shift; the exclusive prefix is resolved first because
+    // the partial outputs are written before the total is known.  A sub-range narrower
+    // than the table holds fewer distinct keys than slots, so the splitting ends.
     if (wid == 0) {
       const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
       if (lane == 0) excl_s = ex;
     }
     if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_overflow), 1ull);
-    // key range of the partition (the all-ones key is counted apart)
     K mn = EMPTY, mx = 0;
     for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
       K key;
@@ -1058,8 +1217,8 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       }
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const K a = shfl_key(mn, (lane + d) & 31), c = shfl_key(mx, (lane + d) & 31);
+    for (int dd = 16; dd > 0; dd >>= 1) {
+      const K a = shfl_key(mn, (lane + dd) & 31), c = shfl_key(mx, (lane + dd) & 31);
       mn = a < mn ? a : mn;
       mx = c > mx ? c : mx;
     }
@@ -1075,14 +1234,17 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         c = red_hi[w] > c ? red_hi[w] : c;
       }
       stk_n = 0;
-      if (a <= c) {  // ranges pop lowest first
+      if (a <= c) {
         stk_lo[0] = a;
         stk_hi[0] = c;
         stk_n = 1;
       }
     }
     __syncthreads();
-    const uint32_t full = (1u << s.bT_max) + (uint32_t)s.tail;
+    const int bTf = s.bT_max;
+    tb.keys = reinterpret_cast<K*>(sm);
+    tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap_slots);
+    dense_layout(bTf, dk, dc, hist, dcap);
     uint64_t written = 0;
     while (stk_n > 0) {
       const K lo = stk_lo[stk_n - 1], hi = stk_hi[stk_n - 1];
@@ -1091,18 +1253,19 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         --stk_n;
         ovf_s = 0;
         special_s = 0;
+        nnew_s = 0;
+        cursor_s = 0;
       }
-      table_clear<KW>(tb, full);
+      table_clear<KW>(tb, cap_slots);
       __syncthreads();
+      count_all<KW>(tb, in, n, true, lo, hi, bTf, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+      __syncthreads();
+      const uint32_t dn2 = nnew_s;
       const K width = hi - lo;
-      const int sh = max(0, bitlen(width) - s.bT_max);
-      insert_all<KW>(tb, in, n, true, lo, hi, full, [&](K key) { return (uint32_t)((key - lo) >> sh); }, &ovf_s,
-                     &special_s, &b.meta->status);
-      __syncthreads();
-      if (ovf_s) {
+      if (ovf_s || dn2 > dcap || dn2 > 16u * kWorkers) {
         if (threadIdx.x == 0) {
-          if (sh == 0 || stk_n + 2 > 160) {
-            atomicOr(&b.meta->status, ST_INTERNAL);  // cannot happen: a narrow range never overflows
+          if (width == 0 || stk_n + 2 > 160) {
+            atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
           } else {
             const K mid = lo + (width >> 1);
             stk_lo[stk_n] = mid + 1;
@@ -1115,9 +1278,27 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         __syncthreads();
         continue;
       }
-      sort_clusters<KW>(tb, full);
+      // stage in the output region this sub-range will occupy, order, write back in place
+      const uint64_t base = excl_s + written;
+      if (base + dn2 > s.cap) {
+        if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+        __syncthreads();
+        continue;
+      }
+      stage_table<KW>(tb, cap_slots, b.out_keys + base * KW, b.out_counts + base, &cursor_s);
       __syncthreads();
-      written += emit_table<KW>(tb, full, true, excl_s + written, b.out_keys, b.out_counts, wcnt, s.cap, &b.meta->status);
+      if (wid > 0) {
+        uint32_t NB = 1;
+        while (NB < 32768u && NB * 2 <= dn2) NB <<= 1;
+        const int bB = ceil_log2_u32(NB);
+        const int sh = max(0, bitlen(width) - bB);
+        order_entries<KW>(b.out_keys + base * KW, b.out_counts + base, dn2, dk, dc, hist, NB,
+                          [&](K key) { return (uint32_t)((key - lo) >> sh); }, big_list, &big_n, wtmp);
+      }
+      __syncthreads();
+      emit_dense<KW>(dk, dc, dn2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+      written += dn2;
+      __syncthreads();
     }
     // the all-ones key, if present, is the largest key of all
     uint32_t sp = 0;
@@ -1127,12 +1308,12 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       sp += key == EMPTY;
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, d);
-    if (lane == 0) wcnt[wid] = sp;
+    for (int dd = 16; dd > 0; dd >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, dd);
+    if (lane == 0) wtmp[wid] = sp;
     __syncthreads();
     if (threadIdx.x == 0) {
       uint64_t tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wcnt[w];
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wtmp[w];
       if (tot) {
         if (tot > 0xffffffffull) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
         if (excl_s + written < s.cap) {
@@ -1146,10 +1327,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       st_release(&b.look[g], kLookIncl | (excl_s + written));
     }
     __syncthreads();
-  }
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    // n_distinct is the inclusive prefix of the last partition; read it after all
-    // partitions published (this block may finish early, so the host derives D instead)
+    phase(6);
   }
 }
 
