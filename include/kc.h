@@ -134,6 +134,36 @@ kc_status kc_last_stats(kc_plan_t plan, kc_stats *out);
  * KC_PLAN_PROFILE). */
 kc_status kc_last_kernel_times(kc_plan_t plan, uint32_t max, const char **names, float *ms, uint32_t *n_out);
 
+/* ---- Counting without allocation -------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that may not
+ * allocate device memory while they count: for example an application that has given all
+ * device memory to its own pool at start-up, or a latency-bound loop where an allocation,
+ * and the synchronisation it can bring, is not acceptable.  It computes exactly what
+ * kc_count computes, with the same kernels, but allocates nothing: every scratch buffer
+ * lives in one fixed device array of KC_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ *   reads, offsets  device memory (reads 16-byte aligned); offsets[n_reads] (the number
+ *                   of bases) at most KC_NOALLOC_MAX_BASES.
+ *   out_keys        device buffer of out_capacity * key_words uint64 (key_words = 1 for
+ *                   k <= 32, else 2, (lo, hi) per key); out_counts: out_capacity uint32.
+ *                   out_capacity must be at least offsets[n_reads].
+ *   n_distinct, n_valid_windows   host pointers, written on success.
+ *   stream          cudaStream_t (NULL = legacy default); the call returns after the
+ *                   result is complete on it.
+ * The first call on a device (with that device current) looks up the scratch array's
+ * device address and sets kernel attributes; make that first call before any stream
+ * capture.  All calls share the one array, and each call clears what it needs: calls
+ * that overlap on the GPU (other streams, other host threads) race and must not be made.
+ * Errors: KC_EINVAL (sizes beyond the maximum, host or misaligned buffers, small
+ * out_capacity, bad k or offsets), KC_ECUDA, KC_EOVERFLOW, KC_ETIMEOUT; kc_last_error()
+ * gives the message. */
+#define KC_NOALLOC_MAX_BASES (1u << 20)
+#define KC_NOALLOC_SCRATCH_BYTES (48u << 20)
+kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, int k, int canonical,
+                           uint64_t *out_keys, uint32_t *out_counts, uint64_t out_capacity, uint64_t *n_distinct,
+                           uint64_t *n_valid_windows, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
-            "kc_last_error", "kc_last_stats", "kc_last_kernel_times"]
+            "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc"]
+KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.kc_last_kernel_times.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)]
     lib.kc_last_kernel_times.restype = i32
+    lib.kc_count_noalloc.argtypes = [vp, vp, u64, i32, i32, vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
+    lib.kc_count_noalloc.restype = i32
     _lib = lib
     return lib
 

@@ -26,6 +26,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+namespace kc {
+void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace kc
+
 struct kc_plan_s {
   int device = 0;
   cudaStream_t stream = nullptr;

@@ -105,6 +105,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
 int configure_kernels(int device);  // sets shared-memory attributes; returns 0 or a cudaError_t
 
 size_t count_kernel_smem(int kw, int bT_max, int tail);
+void set_error_message(const char* msg);  // the text kc_last_error returns on this thread
 int table_log2_max(int kw, size_t smem_optin);
 
 }  // namespace kc
