@@ -124,6 +124,9 @@ typedef struct {
   uint64_t phase_cycles[8];    /* KC_PLAN_PROFILE only: SM cycles of the count kernel's phases
                                   (clear, insert, sort, count, look-back, emit, overflow path,
                                   setup), summed over its thread blocks */
+  uint64_t sub_cycles[8];      /* KC_PLAN_PROFILE only: cycles of the ordering sub-steps (key
+                                  range, rank, scan, place, small sorts, large sorts) and the
+                                  number of large buckets */
 } kc_stats;
 kc_status kc_last_stats(kc_plan_t plan, kc_stats *out);
 

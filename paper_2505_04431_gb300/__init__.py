@@ -52,7 +52,8 @@ class Result(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint32), ("n_partitions", ctypes.c_uint32),
                 ("n_fine", ctypes.c_uint64), ("n_overflow_fine", ctypes.c_uint64),
-                ("workspace_bytes", ctypes.c_uint64), ("phase_cycles", ctypes.c_uint64 * 8)]
+                ("workspace_bytes", ctypes.c_uint64), ("phase_cycles", ctypes.c_uint64 * 8),
+                ("sub_cycles", ctypes.c_uint64 * 8)]
 
 
 class KcError(RuntimeError):
@@ -241,6 +242,7 @@ class KmerCounter:
         _check(self._lib, self._lib.kc_last_stats(self._plan, ctypes.byref(st)))
         out = {f: getattr(st, f) for f, _ in Stats._fields_}
         out["phase_cycles"] = [int(x) for x in st.phase_cycles]
+        out["sub_cycles"] = [int(x) for x in st.sub_cycles]
         return {k: (v if isinstance(v, list) else int(v)) for k, v in out.items()}
 
     def kernel_times(self) -> list[tuple[str, float]]:

@@ -270,7 +270,11 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   s.kw = k <= 32 ? 1 : 2;
   int b1;
   if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
-  else b1 = ceil_log2_u64((L >> 21) + 1) < 10 ? ceil_log2_u64((L >> 21) + 1) : 10;
+  else {
+    // about 8 MB of keys per coarse partition, at most 2048 partitions
+    const int want = ceil_log2_u64((L * (uint64_t)(k <= 32 ? 1 : 2)) / (1u << 20) + 1);
+    b1 = want < 11 ? want : 11;
+  }
   s.b1 = b1;
   const int P1 = 1 << b1;
   int bT_max = kc::table_log2_max(s.kw, p->smem_optin);
@@ -303,6 +307,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   const size_t o_cst = lay.add((size_t)(P1 + 1) * 8);
   const size_t o_fb = lay.add((size_t)(P1 + 1) * 4);
   const size_t o_fl = lay.add((size_t)P1);
+  const size_t o_hll = lay.add((size_t)kc::kHllRegs * 4);
   const size_t o_fh = lay.add((size_t)nf_max * 4);
   const size_t o_fo = lay.add((size_t)(nf_max + 1) * 8);
   const size_t o_fc = lay.add((size_t)nf_max * 8);
@@ -341,6 +346,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   b.cstart = (uint64_t*)(ws + o_cst);
   b.fine_base = (uint32_t*)(ws + o_fb);
   b.fine_log2 = (uint8_t*)(ws + o_fl);
+  b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);
   b.fcur = (unsigned long long*)(ws + o_fc);
@@ -368,6 +374,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
     return bail(KC_ECUDA, std::string("kc_count: copying offsets: ") + cudaGetErrorString(e));
   if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.fhist, 0, (size_t)nf_max * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.look, 0, (size_t)nf_max * 8, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.cstart, 0, (size_t)(P1 + 1) * 8, st)) != cudaSuccess)
     return bail(KC_ECUDA, std::string("kc_count: clearing scratch: ") + cudaGetErrorString(e));
@@ -404,7 +411,10 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   p->stats.n_fine = m.n_fine;
   p->stats.n_overflow_fine = m.n_overflow;
   for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
+  for (int i = 0; i < 8; ++i) p->stats.sub_cycles[i] = m.sub_cycles[i];
   if (m.status & kc::ST_BAD_OFFSETS) return bail(KC_EINVAL, "kc_count: offsets must start at 0 and be non-decreasing");
+  if (m.status & kc::ST_PARTITION_OVERFLOW)
+    return bail(KC_EOVERFLOW, "kc_count: one key range holds 2^32 windows or more; use more partitions");
   if (m.status & kc::ST_COUNT_OVERFLOW) return bail(KC_EOVERFLOW, "kc_count: a count exceeds 2^32 - 1");
   if (m.status & kc::ST_TIMEOUT) return bail(KC_ETIMEOUT, "kc_count: a device-side wait timed out");
   if (m.status & kc::ST_INTERNAL) return bail(KC_ECUDA, "kc_count: internal consistency check failed");

@@ -27,6 +27,10 @@ constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
 constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
 constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
 constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
+constexpr int kHllLog2 = 10;                   // distinct-key sketch: 1024 registers
+constexpr int kHllRegs = 1 << kHllLog2;
+constexpr int kHllSampleLog2 = 3;              // ... over a 1/8 hash sample of the keys
+constexpr double kHllSample = 8.0;
 constexpr uint32_t kLookbackSpinLimit = 1u << 22;  // x ~100 ns sleep: ~0.4 s, then give up
 
 // status bits written by kernels (a kc_status is derived from them on the host)
@@ -35,6 +39,7 @@ enum : uint32_t {
   ST_TIMEOUT = 2u,          // a bounded wait gave up
   ST_BAD_OFFSETS = 4u,      // offsets not non-decreasing
   ST_INTERNAL = 8u,         // an internal consistency check failed
+  ST_PARTITION_OVERFLOW = 16u,  // a coarse partition holds 2^32 keys or more
 };
 
 // Values the host reads back at the end of a call.
@@ -46,6 +51,8 @@ struct Meta {
   uint32_t status;
   uint32_t pad;
   uint64_t ticket;      // phase-2 work counter
+  uint64_t d_estimate;  // distinct keys estimated by the sketch
+  uint64_t sub_cycles[8];    // profiled plans only: ordering sub-steps (range, rank, scan, place, small sorts, big sorts, #big)
   uint64_t phase_cycles[8];  // profiled plans only: SM cycles per phase of k_count_emit, summed over CTAs
 };
 
@@ -78,6 +85,7 @@ struct Buffers {
   uint64_t* cstart;       // [P1 + 1] coarse partition starts
   uint32_t* fine_base;    // [P1 + 1] first fine index of each coarse partition
   uint8_t* fine_log2;     // [P1]
+  uint32_t* hll;          // [kHllRegs] distinct-key sketch (max-merged by pass B)
   uint32_t* fhist;        // [nf_max] keys per fine partition
   uint64_t* foff;         // [nf_max + 1] fine partition starts
   unsigned long long* fcur;  // [nf_max] fine scatter cursors

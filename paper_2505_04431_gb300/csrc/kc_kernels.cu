@@ -57,18 +57,6 @@ __device__ __forceinline__ u128 revcomp(u128 v, int k) {
   u128 r = ((u128)revpairs64(~(uint64_t)v) << 64) | revpairs64(~(uint64_t)(v >> 64));
   return r >> (128 - 2 * k);
 }
-// top 64 bits of a 2k-bit key
-__device__ __forceinline__ uint64_t top64(uint64_t key, int k) { return key << (64 - 2 * k); }
-__device__ __forceinline__ uint64_t top64(u128 key, int k) { return (uint64_t)(key >> (2 * k - 64)); }
-// monotone flattening map (see file comment)
-__device__ __forceinline__ uint64_t utrans(uint64_t x, int canonical) {
-  if (!canonical) return x;
-  const uint64_t y = ~x;
-  return ~__umul64hi(y, y);
-}
-__device__ __forceinline__ uint32_t field(uint64_t u, int skip, int bits) {
-  return bits ? (uint32_t)((u << skip) >> (64 - bits)) : 0u;
-}
 template <class K> __device__ __forceinline__ K all_ones() { return ~(K)0; }
 
 __device__ __forceinline__ uint64_t shfl_key(uint64_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
@@ -78,12 +66,14 @@ __device__ __forceinline__ u128 shfl_key(u128 v, int src) {
   return ((u128)hi << 64) | lo;
 }
 
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// Look-back status words carry their own payload (flag and value in one 64-bit word) and
+// guard no other data, so relaxed GPU-scope accesses are enough.
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -239,48 +229,114 @@ __device__ void build_starts(const uint64_t* offsets, uint64_t n_reads, uint64_t
   if (t == 0) *rcur_s += adv;
 }
 
-// Walk the 32 windows ending in the code word at `slot` (bases q0 .. q0+31); call
-// f(o, key) for every valid window ending at q0 + o.  Slots slot-2, slot-1 hold the two
-// previous words.  Valid: the k bases are ACGT and no read starts after the first of them.
-template <int KW, class F>
-__device__ __forceinline__ void for_windows(const uint64_t* code_s, const uint32_t* inv_s, const uint32_t* st_s, int slot,
-                                            uint64_t q0, uint64_t L, int k, int canonical, F&& f) {
-  typedef typename KeyT<KW>::T K;
-  const K mask = key_mask(K(0), k);
-  K fwd;
-  if constexpr (KW == 1) fwd = (K)code_s[slot - 1] & mask;
-  else fwd = (K)((((u128)code_s[slot - 2]) << 64) | code_s[slot - 1]) & mask;
-  K rc = revcomp(fwd, k);
-  const uint64_t yi = (uint64_t)inv_s[slot - 2] | ((uint64_t)inv_s[slot - 1] << 32);
-  const uint64_t ys = (uint64_t)st_s[slot - 2] | ((uint64_t)st_s[slot - 1] << 32);
-  int run = min(__clzll(yi), __clzll(ys) + 1);
-  const uint64_t w = code_s[slot];
-  const uint32_t iv = inv_s[slot], sv = st_s[slot];
-  const uint64_t left = L - q0;
-  const int nq = left < 32 ? (int)left : 32;
-  const int sh = 2 * k - 2;
-#pragma unroll
-  for (int o = 0; o < 32; ++o) {
-    const uint32_t c = (uint32_t)(w >> (62 - 2 * o)) & 3u;
-    const int ib = (iv >> o) & 1, sb = (sv >> o) & 1;
-    run = ib ? 0 : (sb ? 1 : min(run + 1, 64));
-    fwd = ((fwd << 2) | (K)c) & mask;
-    rc = (rc >> 2) | ((K)(3u - c) << sh);
-    if (o < nq && run >= k) {
-      const K key = (canonical && rc < fwd) ? rc : fwd;
-      f(o, key);
-    }
-  }
+// The range map: coarse partition, fine partition are bit fields of a 32-bit value u,
+// non-decreasing in the key.  x = top 32 bits of the 2k-bit key; canonical keys are the
+// min of two near-independent uniforms (density 2(1-x)), so u = 1 - (1-x)^2 (its
+// distribution function) spreads them evenly.
+__device__ __forceinline__ uint32_t top32_of(uint64_t key, int k) { return (uint32_t)((key << (64 - 2 * k)) >> 32); }
+__device__ __forceinline__ uint32_t top32_of(u128 key, int k) { return (uint32_t)(key >> (2 * k - 32)); }
+__device__ __forceinline__ uint32_t umap(uint32_t x, int canonical) {
+  if (!canonical) return x;
+  const uint32_t y = ~x;
+  return ~__umulhi(y, y);
 }
-
+__device__ __forceinline__ uint32_t field32(uint32_t u, int skip, int bits) {
+  const uint32_t v = skip >= 32 ? 0u : (u << skip);
+  return bits ? v >> (32 - bits) : 0u;
+}
 template <class K>
 __device__ __forceinline__ uint32_t coarse_of(K key, int k, int canonical, int b1) {
-  return field(utrans(top64(key, k), canonical), 0, b1);
+  return field32(umap(top32_of(key, k), canonical), 0, b1);
+}
+
+// Windows of one thread: WPT consecutive window ends starting at base q0 = 32j + 32 - ... see
+// win_setup.  With the base stream S aligned so that window i's first base is S's base i,
+// window i's forward key is the top 2k bits of S << 2i and its reverse complement the top
+// 2k bits of R << 2(WPT-1-i), R being the complemented bases in reverse order.  Both
+// shifts are compile-time constants once the loop over i is unrolled.
+struct Win {
+  uint64_t s0, s1, s2;  // S, left-aligned (192 bits; only s0, s1 used for k <= 32)
+  uint64_t r0, r1, r2;  // R, left-aligned
+  uint64_t m0, m1;      // mask of the top 2k bits (m1 used for k > 32)
+  uint32_t iv, sv;      // invalid / read-start bits of the thread's WPT bases (bit i = base q0 + i)
+  int run;              // valid same-read bases ending at q0 - 1 (capped at 64)
+};
+
+__device__ __forceinline__ uint64_t shl128_hi(uint64_t a, uint64_t b, int sh) {  // top word of (a:b) << sh, 0 <= sh <= 64
+  return sh == 0 ? a : (sh >= 64 ? b : (a << sh) | (b >> (64 - sh)));
+}
+
+// Set up the walk over bases q0 .. q0+WPT-1 of code word j (q0 = 32j + 32 - WPT*(2-h) ... for
+// WPT == 32, q0 = 32j; for WPT == 16, q0 = 32j + 16h).  w2, w1, w0: code words j-2, j-1, j.
+template <int KW, int WPT>
+__device__ __forceinline__ void win_setup(uint64_t w2, uint64_t w1, uint64_t w0, uint32_t i2, uint32_t i1, uint32_t i0,
+                                          uint32_t t2, uint32_t t1, uint32_t t0, int h, int k, Win& W) {
+  // (w2 : w1 : w0) holds bases 32j-64 .. 32j+31; the first window's first base is
+  // q0 - k + 1 = 32j + 16h - k + 1, at index 65 + 16h - k of that string.
+  const int off = 65 + 16 * h - k;  // base index, >= 1
+  const int sh = 2 * off;           // bits to drop from the top, 2 .. 162
+  if (sh >= 128) {
+    W.s0 = w0 << (sh - 128);
+    W.s1 = 0;
+    W.s2 = 0;
+  } else if (sh >= 64) {
+    W.s0 = shl128_hi(w1, w0, sh - 64);
+    W.s1 = (sh - 64 == 0) ? w0 : w0 << (sh - 64);
+    W.s2 = 0;
+  } else {
+    W.s0 = shl128_hi(w2, w1, sh);
+    W.s1 = shl128_hi(w1, w0, sh);
+    W.s2 = w0 << sh;
+  }
+  // R: complements of bases 32j+31 down to 32j-64; window i's reverse complement starts at
+  // base q0 + i, i.e. at index 31 - 16h - i of R, so align R to index 31 - 16h - (WPT - 1).
+  const uint64_t r0 = revpairs64(~w0), r1 = revpairs64(~w1), r2 = revpairs64(~w2);
+  const int rsh = 2 * (32 - 16 * h - WPT);  // 0 (WPT 32 or h 1) or 32 (WPT 16, h 0)
+  W.r0 = shl128_hi(r0, r1, rsh);
+  W.r1 = shl128_hi(r1, r2, rsh);
+  W.r2 = rsh ? r2 << rsh : r2;
+  if (KW == 1) {
+    W.m0 = k >= 32 ? ~0ull : ~(~0ull >> (2 * k));
+    W.m1 = 0;
+  } else {
+    W.m0 = ~0ull;
+    W.m1 = k >= 64 ? ~0ull : ~(~0ull >> (2 * k - 64));
+  }
+  // run length ending at q0 - 1: the 64 mask bits ending there
+  const int lo = 16 * h;  // bit of q0 - 64 within (i2 | i1 << 32 | i0 << 64)
+  const uint64_t yi = lo == 0 ? ((uint64_t)i2 | ((uint64_t)i1 << 32)) : (((uint64_t)i2 >> 16) | ((uint64_t)i1 << 16) | ((uint64_t)i0 << 48));
+  const uint64_t ys = lo == 0 ? ((uint64_t)t2 | ((uint64_t)t1 << 32)) : (((uint64_t)t2 >> 16) | ((uint64_t)t1 << 16) | ((uint64_t)t0 << 48));
+  W.run = min(__clzll(yi), __clzll(ys) + 1);
+  W.iv = i0 >> lo;
+  W.sv = t0 >> lo;
+}
+
+// Window i of a thread's walk: updates the run length, returns true and the key if valid.
+template <int KW, int WPT>
+__device__ __forceinline__ bool win_key(Win& W, int i, int k, int canonical, int nvalid, typename KeyT<KW>::T& key) {
+  const int ib = (W.iv >> i) & 1, sb = (W.sv >> i) & 1;
+  W.run = ib ? 0 : (sb ? 1 : min(W.run + 1, 64));
+  const int fs = 2 * i, rs = 2 * (WPT - 1 - i);
+  if constexpr (KW == 1) {
+    const uint64_t f = shl128_hi(W.s0, W.s1, fs) & W.m0;
+    const uint64_t r = shl128_hi(W.r0, W.r1, rs) & W.m0;
+    const uint64_t c = (canonical && r < f) ? r : f;
+    key = k >= 32 ? c : c >> (64 - 2 * k);
+  } else {
+    const uint64_t f0 = shl128_hi(W.s0, W.s1, fs), f1 = shl128_hi(W.s1, W.s2, fs) & W.m1;
+    const uint64_t r0 = shl128_hi(W.r0, W.r1, rs), r1 = shl128_hi(W.r1, W.r2, rs) & W.m1;
+    const bool rlt = (r0 < f0) || (r0 == f0 && r1 < f1);
+    const u128 c = (canonical && rlt) ? (((u128)r0 << 64) | r1) : (((u128)f0 << 64) | f1);
+    key = k >= 64 ? c : c >> (128 - 2 * k);
+  }
+  return i < nvalid && W.run >= k;
 }
 
 // ------------------------------------------------------------------ pass A
+// One code word per thread: convert, store, and histogram the coarse partitions of its 32
+// windows (keys are recomputed in pass B, which needs the partition offsets first).
 template <int KW>
-__global__ void __launch_bounds__(kPackThreads) k_pack_count(Shape s, Buffers b) {
+__global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ uint32_t hist_s[];  // [P1]
   __shared__ uint64_t code_s[kPackThreads + 2];
@@ -307,29 +363,34 @@ __global__ void __launch_bounds__(kPackThreads) k_pack_count(Shape s, Buffers b)
         inv_s[t] = ~0u;
       }
     }
-    __syncthreads();
     const uint64_t j = j0 + t;
+    uint64_t code = 0;
+    uint32_t inv = ~0u;
     if (j < s.n_words) {
-      uint64_t code;
-      uint32_t inv;
       convert_word(b.reads, s.L, j, code, inv);
       b.codes64[j] = code;
       b.inv32[j] = inv;
-      code_s[t + 2] = code;
-      inv_s[t + 2] = inv;
-    } else {
-      code_s[t + 2] = 0;
-      inv_s[t + 2] = ~0u;
     }
+    __syncthreads();
+    code_s[t + 2] = code;
+    inv_s[t + 2] = inv;
     st_s[t + 2] = 0;
     if (t < 2) st_s[t] = 0;
     __syncthreads();
     build_starts(b.offsets, s.n_reads, j0, kPackThreads, st_s, &rcur_s);
     __syncthreads();
     if (j < s.n_words) {
-      for_windows<KW>(code_s, inv_s, st_s, t + 2, j * 32, s.L, s.k, s.canonical, [&](int, K key) {
-        atomicAdd(&hist_s[coarse_of(key, s.k, s.canonical, s.b1)], 1u);
-      });
+      Win W;
+      win_setup<KW, 32>(code_s[t], code_s[t + 1], code, inv_s[t], inv_s[t + 1], inv, st_s[t], st_s[t + 1], st_s[t + 2],
+                        0, s.k, W);
+      const uint64_t left = s.L - j * 32;
+      const int nvalid = left < 32 ? (int)left : 32;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        K key;
+        if (win_key<KW, 32>(W, i, s.k, s.canonical, nvalid, key))
+          atomicAdd(&hist_s[coarse_of(key, s.k, s.canonical, s.b1)], 1u);
+      }
     }
   }
   __syncthreads();
@@ -368,70 +429,135 @@ __global__ void k_col_scan(const uint32_t* hist, uint64_t* toff, uint64_t* ccoun
   }
 }
 
-// Partition starts, fine split per partition, totals.  One block.
-__global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, uint32_t* fine_base, uint8_t* fine_log2, int P1,
-                              uint32_t fine_target, uint32_t nf_max, Meta* meta) {
-  extern __shared__ uint64_t sc[];  // [P1] then [P1] u64
+// Partition starts and the total number of windows.  One block.
+__global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, Meta* meta) {
+  extern __shared__ uint64_t sc[];  // [P1]
   __shared__ uint64_t wt[32];
-  uint64_t* a = sc;
-  uint64_t* f = sc + P1;
   for (int c = threadIdx.x; c < P1; c += blockDim.x) {
     const uint64_t n = ccount[c];
-    a[c] = n;
-    const uint64_t m = (n + fine_target - 1) / fine_target;
+    sc[c] = n;
+    if (n > 0xffffffffull) atomicOr(&meta->status, ST_PARTITION_OVERFLOW);  // pass B keeps 32-bit cursors
+  }
+  __syncthreads();
+  const uint64_t K = block_exclusive_scan<uint64_t>(sc, P1, wt);
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) cstart[c] = sc[c];
+  if (threadIdx.x == 0) {
+    cstart[P1] = K;
+    meta->n_windows = K;
+  }
+}
+
+// Fine split of every coarse partition, after pass B: the distinct-key estimate (a sampled
+// HyperLogLog filled by pass B) gives the duplication factor K / D, and a fine partition
+// aims at fine_target distinct keys, i.e. fine_target * K / D keys.  One block.
+__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint8_t* fine_log2, int P1,
+                            uint32_t fine_target, uint32_t nf_max, Meta* meta) {
+  extern __shared__ uint64_t fsc[];  // [P1]
+  __shared__ uint64_t wt[32];
+  __shared__ float zsum_s[32], zeros_s[32];
+  __shared__ double target_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // HyperLogLog estimate over the 1/8 hash-sample of the keys
+  float z = 0.f, zeros = 0.f;
+  for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) {
+    const uint32_t r = hll[i];
+    z += exp2f(-(float)r);
+    zeros += r == 0 ? 1.f : 0.f;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    z += __shfl_xor_sync(0xffffffffu, z, d);
+    zeros += __shfl_xor_sync(0xffffffffu, zeros, d);
+  }
+  if (lane == 0) {
+    zsum_s[wid] = z;
+    zeros_s[wid] = zeros;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double zs = 0, zr = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      zs += zsum_s[w];
+      zr += zeros_s[w];
+    }
+    const double m = kHllRegs;
+    double e = 0.7213 / (1.0 + 1.079 / m) * m * m / zs;
+    if (e < 2.5 * m && zr > 0) e = m * log(m / zr);
+    const double d_est = e * kHllSample;
+    const double K = (double)cstart[P1];
+    double dup = d_est > 1.0 ? K / d_est : 1.0;
+    dup = dup < 1.0 ? 1.0 : (dup > 32.0 ? 32.0 : dup);
+    target_s = (double)fine_target * (0.8 * dup > 1.0 ? 0.8 * dup : 1.0);
+    meta->d_estimate = (uint64_t)d_est;
+  }
+  __syncthreads();
+  const double target = target_s;
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) {
+    const uint64_t n = cstart[c + 1] - cstart[c];
+    const uint64_t m = (uint64_t)ceil((double)n / target);
     int bf = m <= 1 ? 0 : 64 - __clzll(m - 1);
     bf = min(bf, kMaxFineLog2);
     fine_log2[c] = (uint8_t)bf;
-    f[c] = 1ull << bf;
+    fsc[c] = 1ull << bf;
   }
   __syncthreads();
-  const uint64_t K = block_exclusive_scan<uint64_t>(a, P1, wt);
-  const uint64_t NF = block_exclusive_scan<uint64_t>(f, P1, wt);
-  for (int c = threadIdx.x; c < P1; c += blockDim.x) {
-    cstart[c] = a[c];
-    fine_base[c] = (uint32_t)f[c];
-  }
+  const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1, wt);
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) fine_base[c] = (uint32_t)fsc[c];
   if (threadIdx.x == 0) {
-    cstart[P1] = K;
     fine_base[P1] = (uint32_t)NF;
-    meta->n_windows = K;
     meta->n_fine = NF <= nf_max ? NF : 0;  // later kernels never index past nf_max
     if (NF > nf_max) atomicOr(&meta->status, ST_INTERNAL);
   }
 }
 
 // ------------------------------------------------------------------ pass B
+// Per sub-step, NT threads x WPT windows: every key is computed once and kept in registers,
+// its rank inside its partition taken with a shared-memory atomic (counting sort, step 1);
+// after the block scan of the partition histogram the keys go to their partition's run in
+// the staging buffer, and the runs leave in order.  A 1/8 hash sample of the keys feeds a
+// HyperLogLog sketch (distinct-key estimate for sizing the fine partitions).
+__device__ __forceinline__ uint64_t key_hash(uint64_t key) { return key * 0x9E3779B97F4A7C15ull; }
+__device__ __forceinline__ uint64_t key_hash(u128 key) {
+  return ((uint64_t)key ^ ((uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
+}
+
 template <int KW, int NT>
-__global__ void __launch_bounds__(NT) k_scatter(Shape s, Buffers b) {
+__global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
-  constexpr int SUB = NT * 32;  // windows per sub-step
+  constexpr int WPT = KW == 1 ? 32 : 16;    // windows per thread
+  constexpr int TPW = 32 / WPT;             // threads per code word
+  constexpr int NW = NT / TPW;              // code words per sub-step
+  constexpr int SUB = NT * WPT;             // windows per sub-step
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
-  K* stage = reinterpret_cast<K*>(sm);                                     // [SUB]
-  uint16_t* stage_c = reinterpret_cast<uint16_t*>(stage + SUB);            // [SUB]
-  uint64_t* cursor = reinterpret_cast<uint64_t*>(stage_c + SUB);           // [P1]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);               // [P1]
-  uint32_t* soff = hist + P1;                                              // [P1]
-  __shared__ uint64_t code_s[NT + 2];
-  __shared__ uint32_t inv_s[NT + 2];
-  __shared__ uint32_t st_s[NT + 2];
+  K* stage = reinterpret_cast<K*>(sm);                               // [SUB]
+  uint16_t* stage_c = reinterpret_cast<uint16_t*>(stage + SUB);      // [SUB]
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(stage_c + SUB);     // [P1], relative to the partition start
+  uint32_t* hist = cursor + P1;                                      // [P1]
+  uint32_t* soff = hist + P1;                                        // [P1]
+  __shared__ uint64_t code_s[NW + 2];
+  __shared__ uint32_t inv_s[NW + 2];
+  __shared__ uint32_t st_s[NW + 2];
+  __shared__ uint32_t hll_s[kHllRegs];
   __shared__ uint64_t rcur_s;
   __shared__ uint32_t wt[32];
   const int t = threadIdx.x;
+  const int wl = t / TPW, h = t % TPW;  // code word of the thread within the sub-step, half
   const uint64_t tile = blockIdx.x;
   for (int c = t; c < P1; c += NT) {
-    cursor[c] = b.cstart[c] + b.toff[tile * P1 + c];
+    cursor[c] = (uint32_t)b.toff[tile * P1 + c];
     hist[c] = 0;
   }
+  for (int i = t; i < kHllRegs; i += NT) hll_s[i] = 0;
   if (t == 0) rcur_s = b.tile_first[tile];
-  for (int sub = 0; sub < kTileWords / NT; ++sub) {
-    const uint64_t j0 = tile * kTileWords + (uint64_t)sub * NT;
+  for (int sub = 0; sub < kTileWords / NW; ++sub) {
+    const uint64_t j0 = tile * kTileWords + (uint64_t)sub * NW;
     if (j0 >= s.n_words) break;
     __syncthreads();
     if (t < 2) {
       if (sub > 0) {
-        code_s[t] = code_s[NT + t];
-        inv_s[t] = inv_s[NT + t];
+        code_s[t] = code_s[NW + t];
+        inv_s[t] = inv_s[NW + t];
       } else if (j0 + t >= 2) {
         code_s[t] = b.codes64[j0 + t - 2];
         inv_s[t] = b.inv32[j0 + t - 2];
@@ -440,45 +566,59 @@ __global__ void __launch_bounds__(NT) k_scatter(Shape s, Buffers b) {
         inv_s[t] = ~0u;
       }
     }
-    __syncthreads();
-    const uint64_t j = j0 + t;
-    if (j < s.n_words) {
-      code_s[t + 2] = b.codes64[j];
-      inv_s[t + 2] = b.inv32[j];
-    } else {
-      code_s[t + 2] = 0;
-      inv_s[t + 2] = ~0u;
+    for (int w = t; w < NW; w += NT) {
+      const uint64_t jw = j0 + w;
+      code_s[w + 2] = jw < s.n_words ? b.codes64[jw] : 0;
+      inv_s[w + 2] = jw < s.n_words ? b.inv32[jw] : ~0u;
+      st_s[w + 2] = 0;
     }
-    st_s[t + 2] = 0;
     if (t < 2) st_s[t] = 0;
     __syncthreads();
-    build_starts(b.offsets, s.n_reads, j0, NT, st_s, &rcur_s);
+    build_starts(b.offsets, s.n_reads, j0, NW, st_s, &rcur_s);
     __syncthreads();
-    // rank of every window inside its partition (shared-memory counting sort, step 1)
-    uint32_t rr[16];
+    const uint64_t j = j0 + wl;
+    K keys[WPT];
+    uint32_t rr[WPT / 2];
+    uint32_t valid = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) rr[i] = 0;
+    for (int i = 0; i < WPT / 2; ++i) rr[i] = 0;
     if (j < s.n_words) {
-      for_windows<KW>(code_s, inv_s, st_s, t + 2, j * 32, s.L, s.k, s.canonical, [&](int o, K key) {
-        const uint32_t r = atomicAdd(&hist[coarse_of(key, s.k, s.canonical, s.b1)], 1u);
-        rr[o >> 1] |= r << (16 * (o & 1));
-      });
+      Win W;
+      const int sw = wl + 2;
+      win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], inv_s[sw - 2], inv_s[sw - 1], inv_s[sw],
+                         st_s[sw - 2], st_s[sw - 1], st_s[sw], h, s.k, W);
+      const uint64_t q0 = j * 32 + (uint64_t)(WPT == 16 ? 16 * h : 0);
+      const int nvalid = q0 >= s.L ? 0 : (s.L - q0 < (uint64_t)WPT ? (int)(s.L - q0) : WPT);
+#pragma unroll
+      for (int i = 0; i < WPT; ++i) {
+        if (win_key<KW, WPT>(W, i, s.k, s.canonical, nvalid, keys[i])) {
+          valid |= 1u << i;
+          const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);
+          const uint32_t r = atomicAdd(&hist[c], 1u);
+          rr[i >> 1] |= r << (16 * (i & 1));
+          const uint64_t hh = key_hash(keys[i]);
+          if ((hh >> (64 - kHllSampleLog2)) == 0) {
+            const uint32_t reg = (uint32_t)(hh >> (64 - kHllSampleLog2 - kHllLog2)) & (kHllRegs - 1);
+            const uint64_t rest = hh << (kHllSampleLog2 + kHllLog2);
+            atomicMax(&hll_s[reg], (uint32_t)min(__clzll(rest) + 1, 64 - kHllSampleLog2 - kHllLog2 + 1));
+          }
+        }
+      }
     }
     __syncthreads();
     for (int c = t; c < P1; c += NT) soff[c] = hist[c];
     __syncthreads();
     block_exclusive_scan<uint32_t>(soff, P1, wt);
-    // step 2: place every key at its partition's run in the staging buffer
-    if (j < s.n_words) {
-      for_windows<KW>(code_s, inv_s, st_s, t + 2, j * 32, s.L, s.k, s.canonical, [&](int o, K key) {
-        const uint32_t c = coarse_of(key, s.k, s.canonical, s.b1);
-        const uint32_t pos = soff[c] + ((rr[o >> 1] >> (16 * (o & 1))) & 0xffffu);
-        stage[pos] = key;
+#pragma unroll
+    for (int i = 0; i < WPT; ++i) {
+      if (valid & (1u << i)) {
+        const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);
+        const uint32_t pos = soff[c] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+        stage[pos] = keys[i];
         stage_c[pos] = (uint16_t)c;
-      });
+      }
     }
     __syncthreads();
-    // step 3: runs leave in order, consecutive threads on consecutive addresses
     const uint32_t n_sub = soff[P1 - 1] + hist[P1 - 1];
     for (uint32_t i = t; i < n_sub; i += NT) {
       const uint32_t c = stage_c[i];
@@ -486,7 +626,7 @@ __global__ void __launch_bounds__(NT) k_scatter(Shape s, Buffers b) {
         atomicOr(&b.meta->status, ST_INTERNAL);
         continue;
       }
-      const uint64_t pos = cursor[c] + (i - soff[c]);
+      const uint64_t pos = b.cstart[c] + cursor[c] + (i - soff[c]);
       if (pos < s.cap) store_key(b.kbuf, pos, stage[i]);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
@@ -496,6 +636,9 @@ __global__ void __launch_bounds__(NT) k_scatter(Shape s, Buffers b) {
       hist[c] = 0;
     }
   }
+  __syncthreads();
+  for (int i = t; i < kHllRegs; i += NT)
+    if (hll_s[i]) atomicMax(&b.hll[i], hll_s[i]);
 }
 
 // ------------------------------------------------------------------ phase 2: fine split
@@ -505,9 +648,9 @@ struct FineCtx {
 
 template <class K>
 __device__ __forceinline__ uint32_t fine_index(K key, const FineCtx& x, const uint32_t* fine_base_s, const uint8_t* flog_s) {
-  const uint64_t u = utrans(top64(key, x.k), x.canonical);
-  const uint32_t c = field(u, 0, x.b1);
-  return fine_base_s[c] + field(u, x.b1, flog_s[c]);
+  const uint32_t u = umap(top32_of(key, x.k), x.canonical);
+  const uint32_t c = field32(u, 0, x.b1);
+  return fine_base_s[c] + field32(u, x.b1, flog_s[c]);
 }
 
 template <int KW>
@@ -741,7 +884,7 @@ __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* sta
     uint64_t v = kLookIncl;  // before the first partition: inclusive prefix 0
     if (idx >= 0) {
       uint32_t spins = 0;
-      v = ld_acquire(&look[idx]);
+      v = ld_status(&look[idx]);
       while ((v >> 62) == 0) {
         if (++spins > kLookbackSpinLimit) {
           atomicOr(status, ST_TIMEOUT);
@@ -749,7 +892,7 @@ __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* sta
           break;
         }
         __nanosleep(64);
-        v = ld_acquire(&look[idx]);
+        v = ld_status(&look[idx]);
       }
     }
     const unsigned incl = __ballot_sync(0xffffffffu, (v >> 62) == 2);
@@ -771,24 +914,27 @@ struct Table {
   uint32_t* counts;
 };
 
-// Count kernel shared memory: a hash table of 2^bT_max slots (key + count).  After the
-// count, the same bytes hold the dense array of distinct keys (at most 3/4 of the slots)
-// and the bucket histogram used to order them.
+// Count kernel shared memory: a hash table of 2^bT_max slots (key + count) and a bucket
+// histogram of kHistMax(kw) entries.  After the count, the table's bytes hold the dense
+// array of distinct keys (at most 3/4 of the slots).
+constexpr int kTableLog2Cap = 13;  // 8192 slots: 8 per thread of the 1024-thread block
+__host__ __device__ constexpr int hist_max(int kw) { return kw == 1 ? 16384 : 8192; }
+
 size_t count_kernel_smem(int kw, int bT_max, int /*unused*/) {
   const size_t slots = (size_t)1 << bT_max;
-  return slots * (size_t)(kw * 8 + 4) + 256;
+  return slots * (size_t)(kw * 8 + 4) + (size_t)hist_max(kw) * 4 + 256;
 }
 
 int table_log2_max(int kw, size_t smem_optin) {
   int best = 6;
-  for (int bt = 6; bt <= 16; ++bt)
+  for (int bt = 6; bt <= kTableLog2Cap; ++bt)
     if (count_kernel_smem(kw, bt, 0) + 8192 <= smem_optin) best = bt;  // 8 KB for static shared memory
   return best;
 }
 
 constexpr int kProbeLimit = 128;
-constexpr int kWorkers = kCountThreads - 32;  // warps 1.. order and sort while warp 0 looks back
-constexpr int kBigCap = 256;                  // buckets too large for one thread, sorted per warp
+constexpr int kWorkers = kCountThreads - 32;  // warps 1.. load and sort while warp 0 looks back
+constexpr int kSlotsPerThread = (1 << kTableLog2Cap) / kCountThreads;
 
 // counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes)
 __device__ __forceinline__ uint32_t hslot(uint64_t key, int bT) {
@@ -852,20 +998,21 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
                           typename KeyT<KW>::T hi, int bT, uint32_t* n_new, uint32_t* ovf, uint32_t* special,
                           uint32_t* status) {
   typedef typename KeyT<KW>::T K;
+  constexpr int kIn = KW == 1 ? 4 : 2;  // loads in flight per thread
   const K EMPTY = all_ones<K>();
   const int lane = threadIdx.x & 31;
-  for (uint64_t base = 0; base < n; base += 2 * (uint64_t)blockDim.x) {
-    K kk[2];
-    bool aa[2];
+  for (uint64_t base = 0; base < n; base += kIn * (uint64_t)blockDim.x) {
+    K kk[kIn];
+    bool aa[kIn];
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {  // two loads in flight per thread
+    for (int m = 0; m < kIn; ++m) {
       const uint64_t i = base + (uint64_t)m * blockDim.x + threadIdx.x;
       kk[m] = 0;
       aa[m] = i < n;
       if (aa[m]) load_key(in, i, kk[m]);
     }
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < kIn; ++m) {
       const K key = kk[m];
       bool act = aa[m];
       if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
@@ -894,63 +1041,81 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
   }
 }
 
-// Write the occupied slots (unordered) to stage_keys / stage_counts[0, d).
+template <class K> __device__ __forceinline__ int bitlen(K v);
+template <> __device__ __forceinline__ int bitlen(uint64_t v) { return 64 - __clzll(v); }
+template <> __device__ __forceinline__ int bitlen(u128 v) {
+  const uint64_t hi = (uint64_t)(v >> 64);
+  return hi ? 128 - __clzll(hi) : 64 - __clzll((uint64_t)v);
+}
+
+// Smallest and largest key in the table (all threads; the result is returned to all).
 template <int KW>
-__device__ void stage_table(Table<KW> tb, uint32_t nslots, uint64_t* stage_keys, uint32_t* stage_counts,
-                            uint32_t* cursor) {
+__device__ void table_range(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T* red_lo, typename KeyT<KW>::T* red_hi,
+                            typename KeyT<KW>::T& lo, typename KeyT<KW>::T& hi) {
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
-  const int lane = threadIdx.x & 31;
-  for (uint32_t base = (threadIdx.x & ~31u); base < nslots; base += blockDim.x) {
-    const uint32_t s = base + lane;
-    const bool occ = s < nslots && tb.keys[s] != EMPTY;
-    const unsigned m = __ballot_sync(0xffffffffu, occ);
-    uint32_t pos = 0;
-    if (lane == 0 && m) pos = atomicAdd(cursor, __popc(m));
-    pos = __shfl_sync(0xffffffffu, pos, 0);
-    if (occ) {
-      const uint32_t o = pos + __popc(m & ((1u << lane) - 1));
-      store_key(stage_keys, o, tb.keys[s]);
-      stage_counts[o] = tb.counts[s];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  K mn = EMPTY, mx = 0;
+  for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) {
+    const K key = tb.keys[s];
+    if (key != EMPTY) {
+      mn = key < mn ? key : mn;
+      mx = key > mx ? key : mx;
     }
+  }
+#pragma unroll
+  for (int dd = 16; dd > 0; dd >>= 1) {
+    const K a = shfl_key(mn, (lane + dd) & 31), c = shfl_key(mx, (lane + dd) & 31);
+    mn = a < mn ? a : mn;
+    mx = c > mx ? c : mx;
+  }
+  if (lane == 0) {
+    red_lo[wid] = mn;
+    red_hi[wid] = mx;
+  }
+  __syncthreads();
+  lo = red_lo[0];
+  hi = red_hi[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    lo = red_lo[w] < lo ? red_lo[w] : lo;
+    hi = red_hi[w] > hi ? red_hi[w] : hi;
   }
 }
 
-// Exclusive scan of data[0, n) by the worker threads (named barrier 1); returns the total.
-template <typename T>
-__device__ T workers_exclusive_scan(T* data, int n, T* warp_tmp) {
-  const int t = threadIdx.x - 32, nt = kWorkers, lane = t & 31, wid = t >> 5, nw = kWorkers / 32;
-  const int per = (n + nt - 1) / nt;
-  const int lo = min(n, t * per), hi = min(n, lo + per);
-  T s = 0;
-  for (int i = lo; i < hi; ++i) s += data[i];
-  T x = s;
+// Write the table's entries to stage[0, d) grouped by bucket (key - lo) >> sh, buckets in
+// ascending order (an ordered counting sort; entries inside a bucket are unordered).
+// hist[0, NB) must be zero on entry; on return it holds each bucket's first position.
+// All threads; nslots <= kSlotsPerThread * blockDim.x.
+template <int KW>
+__device__ void place_entries(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T lo, int sh, uint32_t* hist,
+                              uint32_t NB, uint64_t* stage_keys, uint32_t* stage_counts, uint32_t* wtmp) {
+  typedef typename KeyT<KW>::T K;
+  const K EMPTY = all_ones<K>();
+  uint32_t br[kSlotsPerThread];
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) warp_tmp[wid] = x;
-  bar_workers();
-  if (wid == 0) {
-    T w = lane < nw ? warp_tmp[lane] : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= d) w += y;
+  for (int m = 0; m < kSlotsPerThread; ++m) {
+    const uint32_t s = threadIdx.x + m * blockDim.x;
+    br[m] = 0xffffffffu;
+    if (s < nslots) {
+      const K key = tb.keys[s];
+      if (key != EMPTY) {
+        const uint32_t bk = (uint32_t)((key - lo) >> sh);
+        br[m] = (bk << 16) | atomicAdd(&hist[bk], 1u);  // NB <= 2^14, rank < 2^16
+      }
     }
-    if (lane < nw) warp_tmp[lane] = w;
   }
-  bar_workers();
-  T run = x - s + (wid ? warp_tmp[wid - 1] : 0);
-  const T total = warp_tmp[nw - 1];
-  for (int i = lo; i < hi; ++i) {
-    T v = data[i];
-    data[i] = run;
-    run += v;
+  __syncthreads();
+  block_exclusive_scan<uint32_t>(hist, (int)NB, wtmp);
+#pragma unroll
+  for (int m = 0; m < kSlotsPerThread; ++m) {
+    if (br[m] != 0xffffffffu) {
+      const uint32_t s = threadIdx.x + m * blockDim.x;
+      const uint32_t pos = hist[br[m] >> 16] + (br[m] & 0xffffu);
+      store_key(stage_keys, pos, tb.keys[s]);
+      stage_counts[pos] = tb.counts[s];
+    }
   }
-  bar_workers();
-  return total;
+  __syncthreads();
 }
 
 // Sort keys[a, a+c) (with their counts) by one warp: a bitonic network whose comparators
@@ -980,102 +1145,152 @@ __device__ void warp_sort_segment(K* keys, uint32_t* counts, uint32_t a, uint32_
   }
 }
 
-// Order the d staged entries by key into dense_keys / dense_counts (shared memory):
-// an ordered counting sort into NB buckets (bucket = bfn(key), non-decreasing in the
-// key), then a sort inside every bucket.  Run by the worker warps only.
-template <int KW, class B>
-__device__ void order_entries(const uint64_t* stage_keys, const uint32_t* stage_counts, uint32_t d,
-                              typename KeyT<KW>::T* dense_keys, uint32_t* dense_counts, uint32_t* hist, uint32_t NB,
-                              B&& bfn, uint32_t* big_list, uint32_t* big_n, uint32_t* warp_tmp) {
-  typedef typename KeyT<KW>::T K;
-  const int t = threadIdx.x - 32;
-  for (uint32_t i = t; i < NB; i += kWorkers) hist[i] = 0;
-  if (t == 0) *big_n = 0;
-  bar_workers();
-  constexpr int kMaxPer = 16;  // d <= kMaxPer * kWorkers (checked by the caller)
-  uint32_t br[kMaxPer];
+__device__ __forceinline__ uint64_t shfl_xor_key(uint64_t v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ u128 shfl_xor_key(u128 v, int m) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, m);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), m);
+  return ((u128)hi << 64) | lo;
+}
+
+// Sort keys[a, a+c), c <= 32, with their counts: one entry per lane, a bitonic network on
+// shuffles (lanes past c hold the largest key and stay at the end).  Whole warp calls it.
+template <class K>
+__device__ __forceinline__ void warp_sort32(K* keys, uint32_t* counts, uint32_t a, uint32_t c) {
+  const int lane = threadIdx.x & 31;
+  const bool have = (uint32_t)lane < c;
+  K key = have ? keys[a + lane] : ~(K)0;
+  uint32_t cnt = have ? counts[a + lane] : 0u;
 #pragma unroll
-  for (int m = 0; m < kMaxPer; ++m) {
-    const uint32_t i = t + m * kWorkers;
-    br[m] = 0xffffffffu;
-    if (i < d) {
-      K key;
-      load_key(stage_keys, i, key);
-      const uint32_t bk = bfn(key);
-      const uint32_t r = atomicAdd(&hist[bk], 1u);
-      br[m] = (bk << 16) | r;  // NB <= 2^15 buckets, rank < 2^16
-    }
-  }
-  bar_workers();
-  // bucket sizes are kept in the second half of hist's space? no: scan in place, sizes recomputed below
-  workers_exclusive_scan<uint32_t>(hist, (int)NB, warp_tmp);
+  for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
-  for (int m = 0; m < kMaxPer; ++m) {
-    const uint32_t i = t + m * kWorkers;
-    if (i < d) {
-      K key;
-      load_key(stage_keys, i, key);
-      const uint32_t pos = hist[br[m] >> 16] + (br[m] & 0xffffu);
-      dense_keys[pos] = key;
-      dense_counts[pos] = stage_counts[i];
-    }
-  }
-  bar_workers();
-  // sort inside buckets: short ones by one thread, long ones queued for a warp
-  for (uint32_t bk = t; bk < NB; bk += kWorkers) {
-    const uint32_t a = hist[bk];
-    const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
-    const uint32_t c = e - a;
-    if (c < 2) continue;
-    if (c > 32) {
-      const uint32_t q = atomicAdd(big_n, 1u);
-      if (q < kBigCap) {
-        big_list[q] = bk;
-        continue;
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const K other = shfl_xor_key(key, j);
+      const uint32_t oc = __shfl_xor_sync(0xffffffffu, cnt, j);
+      const bool up = (lane & size) == 0, lower = (lane & j) == 0;
+      const bool take = (lower == up) ? (other < key) : (key < other);
+      if (take) {
+        key = other;
+        cnt = oc;
       }
     }
-    for (uint32_t i = a + 1; i < e; ++i) {
-      const K kv = dense_keys[i];
-      const uint32_t cv = dense_counts[i];
-      uint32_t m = i;
-      while (m > a && dense_keys[m - 1] > kv) {
-        dense_keys[m] = dense_keys[m - 1];
-        dense_counts[m] = dense_counts[m - 1];
-        --m;
-      }
-      dense_keys[m] = kv;
-      dense_counts[m] = cv;
-    }
   }
-  bar_workers();
-  const uint32_t nbig = min(*big_n, (uint32_t)kBigCap);
-  for (uint32_t q = (uint32_t)(t >> 5); q < nbig; q += kWorkers / 32) {
-    const uint32_t bk = big_list[q];
-    const uint32_t a = hist[bk];
-    const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
-    warp_sort_segment<K>(dense_keys, dense_counts, a, e - a);
+  if (have) {
+    keys[a + lane] = key;
+    counts[a + lane] = cnt;
   }
 }
 
-// Coalesced copy of the dense sorted entries to out[base, base + d).
+constexpr int kRankPer = 7;        // entries per worker thread: 7 * 992 >= 3/4 of 8192 slots
+constexpr uint32_t kBigBucket = 256;  // buckets above this are sorted in place by a warp first
+
+// Worker warps: read the bucket-grouped staged entries into the dense shared arrays, then
+// give every entry its rank inside the partition: its bucket's first position plus the
+// number of smaller keys in the same bucket (buckets are small; the rare bucket above
+// kBigBucket entries is sorted in place by one warp and ranked by position).
 template <int KW>
-__device__ void emit_dense(const typename KeyT<KW>::T* dense_keys, const uint32_t* dense_counts, uint32_t d,
-                           uint64_t base, uint64_t* out_keys, uint32_t* out_counts, uint64_t cap, uint32_t* status) {
+__device__ __forceinline__ void load_and_rank(const uint64_t* stage_keys, const uint32_t* stage_counts, uint32_t d,
+                                              typename KeyT<KW>::T* dense_keys, uint32_t* dense_counts,
+                                              const uint32_t* hist, uint32_t NB, typename KeyT<KW>::T lo, int sh,
+                                              uint32_t (&rank)[kRankPer], unsigned long long* prof) {
+  typedef typename KeyT<KW>::T K;
+  const int t = threadIdx.x - 32, wid = t >> 5, lane = t & 31;
+  long long tm = clock64();
+  for (uint32_t i = t; i < d; i += kWorkers) {
+    K key;
+    load_key(stage_keys, i, key);
+    dense_keys[i] = key;
+    dense_counts[i] = stage_counts[i];
+  }
+  bar_workers();
+  // rare large buckets: one warp each, in place (each warp scans a slice of the buckets)
+  constexpr int kWarps = kWorkers / 32;
+  const uint32_t per = (NB + kWarps - 1) / kWarps;
+  const uint32_t b_lo = min(NB, (uint32_t)wid * per), b_hi = min(NB, b_lo + per);
+  for (uint32_t base = b_lo; base < b_hi; base += 32) {
+    const uint32_t bk = base + lane;
+    uint32_t a = 0, c = 0;
+    if (bk < b_hi) {
+      a = hist[bk];
+      c = (bk + 1 < NB ? hist[bk + 1] : d) - a;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, c > kBigBucket);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      warp_sort_segment<K>(dense_keys, dense_counts, __shfl_sync(0xffffffffu, a, src),
+                           __shfl_sync(0xffffffffu, c, src));
+    }
+  }
+  bar_workers();
+  if (prof && t == 0) {
+    const long long now = clock64();
+    atomicAdd(&prof[3], (unsigned long long)(now - tm));
+    tm = now;
+  }
+#pragma unroll
+  for (int m = 0; m < kRankPer; ++m) {
+    const uint32_t i = t + m * kWorkers;
+    rank[m] = 0xffffffffu;
+    if (i < d) {
+      const K key = dense_keys[i];
+      const uint32_t bk = (uint32_t)((key - lo) >> sh);
+      const uint32_t a = hist[bk];
+      const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
+      uint32_t r = a;
+      if (e - a > kBigBucket) {
+        r = i;
+      } else {
+        for (uint32_t j = a; j < e; ++j) r += dense_keys[j] < key;
+      }
+      rank[m] = r;
+    }
+  }
+  if (prof && t == 0) atomicAdd(&prof[4], (unsigned long long)(clock64() - tm));
+}
+
+// Worker threads: write their entries at out[base + rank].
+template <int KW>
+__device__ __forceinline__ void emit_ranked(const typename KeyT<KW>::T* dense_keys, const uint32_t* dense_counts,
+                                            uint32_t d, const uint32_t (&rank)[kRankPer], uint64_t base,
+                                            uint64_t* out_keys, uint32_t* out_counts, uint64_t cap, uint32_t* status) {
+  const int t = threadIdx.x - 32;
   if (base + d > cap) {
-    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
+    if (t == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
-  for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
-    store_key(out_keys, base + i, dense_keys[i]);
-    out_counts[base + i] = dense_counts[i];
+#pragma unroll
+  for (int m = 0; m < kRankPer; ++m) {
+    const uint32_t i = t + m * kWorkers;
+    if (i < d && rank[m] < d) {
+      store_key(out_keys, base + rank[m], dense_keys[i]);
+      out_counts[base + rank[m]] = dense_counts[i];
+    }
   }
 }
 
-template <class K> __device__ __forceinline__ int bitlen(K v);
-template <> __device__ __forceinline__ int bitlen(uint64_t v) { return 64 - __clzll(v); }
-template <> __device__ __forceinline__ int bitlen(u128 v) {
-  const uint64_t hi = (uint64_t)(v >> 64);
-  return hi ? 128 - __clzll(hi) : 64 - __clzll((uint64_t)v);
+// Key range of the current table and an ordered counting sort of its entries into NB
+// buckets, written to `stage` (global) grouped by bucket.  All threads.
+template <int KW>
+__device__ void bucket_table(Table<KW> tb, uint32_t nslots, uint32_t d, uint64_t* stage_keys, uint32_t* stage_counts,
+                             uint32_t* hist, typename KeyT<KW>::T* red_lo, typename KeyT<KW>::T* red_hi, uint32_t* wtmp,
+                             unsigned long long* prof, typename KeyT<KW>::T& lo, int& sh, uint32_t& NB) {
+  typedef typename KeyT<KW>::T K;
+  long long tm = clock64();
+  K hi;
+  table_range<KW>(tb, nslots, red_lo, red_hi, lo, hi);
+  NB = 1;
+  while (NB < (uint32_t)hist_max(KW) && NB < 2 * d) NB <<= 1;  // at most two entries per bucket on average
+  const int bB = 31 - __clz(NB);
+  sh = d == 0 ? 0 : max(0, bitlen(K(hi - lo)) - bB);
+  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  if (prof && threadIdx.x == 0) {
+    const long long now = clock64();
+    atomicAdd(&prof[0], (unsigned long long)(now - tm));
+    tm = now;
+  }
+  place_entries<KW>(tb, nslots, lo, sh, hist, NB, stage_keys, stage_counts, wtmp);
+  if (prof && threadIdx.x == 0) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
 }
 
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
@@ -1085,20 +1300,20 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const uint32_t cap_slots = 1u << s.bT_max;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(sm + (size_t)cap_slots * (KW * 8 + 4));
   __shared__ uint64_t g_s, excl_s;
-  __shared__ uint32_t ovf_s, special_s, nnew_s, cursor_s, c_s, flog_s, big_n;
+  __shared__ uint32_t ovf_s, special_s, nnew_s;
   __shared__ uint32_t wtmp[32];
-  __shared__ uint32_t big_list[kBigCap];
   __shared__ K red_lo[32], red_hi[32];
   __shared__ K stk_lo[160], stk_hi[160];
   __shared__ int stk_n;
   const K EMPTY = all_ones<K>();
-  const int P1 = 1 << s.b1;
   const uint64_t NF = b.meta->n_fine;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* stage_cnt_all = reinterpret_cast<uint32_t*>(b.kbuf);  // kbuf is free once the fine split is done
-  // profiled plans: thread 0 adds the cycles spent in each phase (0 clear, 1 count, 2 stage,
-  // 3 order + sort, 4 look-back, 5 emit, 6 overflow path, 7 ticket + setup)
+  unsigned long long* prof = s.profile ? reinterpret_cast<unsigned long long*>(b.meta->sub_cycles) : nullptr;
+  // profiled plans: thread 0 adds the cycles spent in each phase (0 clear, 1 count, 2 -,
+  // 3 order, 4 look-back (warp 0, overlapped), 5 emit, 6 overflow path, 7 ticket + setup)
   long long t_mark = clock64();
   auto phase = [&](int i) {
     if (s.profile && threadIdx.x == 0) {
@@ -1107,20 +1322,16 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       t_mark = now;
     }
   };
-  // the dense array and histogram reuse the table bytes: layout for a table of 2^bT slots
-  auto dense_layout = [&](int bT, K*& dk, uint32_t*& dc, uint32_t*& hist, uint32_t& dcap) {
-    dcap = (3u << bT) >> 2;
-    dk = reinterpret_cast<K*>(sm);
-    dc = reinterpret_cast<uint32_t*>(dk + dcap);
-    hist = dc + dcap;
-  };
+  // dense arrays reuse the table bytes: at most 3/4 of the slots
+  const uint32_t dcap = (3u * cap_slots) >> 2;
+  K* dk = reinterpret_cast<K*>(sm);
+  uint32_t* dc = reinterpret_cast<uint32_t*>(dk + dcap);
   while (true) {
     if (threadIdx.x == 0) {
       g_s = atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->ticket), 1ull);
       ovf_s = 0;
       special_s = 0;
       nnew_s = 0;
-      cursor_s = 0;
     }
     __syncthreads();
     const uint64_t g = g_s;
@@ -1132,15 +1343,6 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       n = 0;
     }
     const uint64_t* in = b.sbuf + f0 * KW;
-    if (threadIdx.x == 0) {  // coarse partition of g: last c with fine_base[c] <= g
-      int lo = 0, hi = P1 - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.fine_base[mid] <= (uint32_t)g) lo = mid; else hi = mid - 1;
-      }
-      c_s = (uint32_t)lo;
-      flog_s = b.fine_log2[lo];
-    }
     // table: at least twice the keys (at most that many distinct), within the cap
     int bT = 6;
     while (bT < s.bT_max && ((uint64_t)1 << bT) < 2 * n) ++bT;
@@ -1154,37 +1356,33 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     count_all<KW>(tb, in, n, false, K(0), K(0), bT, &nnew_s, &ovf_s, &special_s, &b.meta->status);
     __syncthreads();
     phase(1);
-    K* dk;
-    uint32_t *dc, *hist, dcap;
-    dense_layout(bT, dk, dc, hist, dcap);
     const uint32_t dn = nnew_s;
-    if (!ovf_s && dn <= dcap && dn <= 16u * kWorkers) {
+    if (!ovf_s && dn <= dcap) {
       const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
-      if (threadIdx.x == 0) st_release(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
-      // stage the distinct entries in this partition's spent input region
-      stage_table<KW>(tb, 1u << bT, b.sbuf + f0 * KW, stage_cnt_all + f0, &cursor_s);
-      __syncthreads();
-      phase(2);
+      if (threadIdx.x == 0) st_status(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
+      // order through this partition's spent input region (keys) and kbuf (counts)
+      K lo;
+      int sh;
+      uint32_t NB;
+      uint32_t rank[kRankPer];
+      bucket_table<KW>(tb, 1u << bT, dn, b.sbuf + f0 * KW, stage_cnt_all + f0, hist, red_lo, red_hi, wtmp, prof, lo, sh,
+                       NB);
       if (wid == 0) {
+        const long long lb0 = clock64();
         const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
         if (lane == 0) {
-          if (g > 0) st_release(&b.look[g], kLookIncl | (ex + d));
+          if (g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
           excl_s = ex;
+          if (s.profile)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[4]), (unsigned long long)(clock64() - lb0));
         }
       } else {
-        uint32_t NB = 1;
-        while (NB < 32768u && NB * 2 <= dn) NB <<= 1;  // about two entries per bucket
-        const int bB = ceil_log2_u32(NB);
-        const int skip = s.b1 + (int)flog_s;
-        const int kk = s.k, canon = s.canonical;
-        order_entries<KW>(b.sbuf + f0 * KW, stage_cnt_all + f0, dn, dk, dc, hist, NB,
-                          [&](K key) { return field(utrans(top64(key, kk), canon), skip, bB); }, big_list, &big_n,
-                          wtmp);
+        load_and_rank<KW>(b.sbuf + f0 * KW, stage_cnt_all + f0, dn, dk, dc, hist, NB, lo, sh, rank, prof);
       }
       __syncthreads();
       phase(3);
       const uint64_t ex = excl_s;
-      emit_dense<KW>(dk, dc, dn, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+      if (wid > 0) emit_ranked<KW>(dk, dc, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       if (special_s && threadIdx.x == 0) {
         if (ex + dn < s.cap) {
           store_key(b.out_keys, ex + dn, EMPTY);
@@ -1198,10 +1396,10 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       continue;
     }
     // ---------------- overflow path: too many distinct keys for the table.  Split the
-    // partition's key range into sub-ranges, each counted in its own table and ordered
-    // with buckets (key - lo) >> shift; the exclusive prefix is resolved first because
-    // the partial outputs are written before the total is known.  A sub-range narrower
-    // than the table holds fewer distinct keys than slots, so the splitting ends.
+    // partition's key range into sub-ranges, each counted in its own table and ordered;
+    // the exclusive prefix is resolved first because the partial outputs are written
+    // before the total is known.  A sub-range narrower than the table holds fewer
+    // distinct keys than slots, so the splitting ends.
     if (wid == 0) {
       const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
       if (lane == 0) excl_s = ex;
@@ -1244,7 +1442,6 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     const int bTf = s.bT_max;
     tb.keys = reinterpret_cast<K*>(sm);
     tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap_slots);
-    dense_layout(bTf, dk, dc, hist, dcap);
     uint64_t written = 0;
     while (stk_n > 0) {
       const K lo = stk_lo[stk_n - 1], hi = stk_hi[stk_n - 1];
@@ -1254,7 +1451,6 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         ovf_s = 0;
         special_s = 0;
         nnew_s = 0;
-        cursor_s = 0;
       }
       table_clear<KW>(tb, cap_slots);
       __syncthreads();
@@ -1262,7 +1458,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       __syncthreads();
       const uint32_t dn2 = nnew_s;
       const K width = hi - lo;
-      if (ovf_s || dn2 > dcap || dn2 > 16u * kWorkers) {
+      if (ovf_s || dn2 > dcap) {
         if (threadIdx.x == 0) {
           if (width == 0 || stk_n + 2 > 160) {
             atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
@@ -1285,18 +1481,19 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         __syncthreads();
         continue;
       }
-      stage_table<KW>(tb, cap_slots, b.out_keys + base * KW, b.out_counts + base, &cursor_s);
-      __syncthreads();
-      if (wid > 0) {
-        uint32_t NB = 1;
-        while (NB < 32768u && NB * 2 <= dn2) NB <<= 1;
-        const int bB = ceil_log2_u32(NB);
-        const int sh = max(0, bitlen(width) - bB);
-        order_entries<KW>(b.out_keys + base * KW, b.out_counts + base, dn2, dk, dc, hist, NB,
-                          [&](K key) { return (uint32_t)((key - lo) >> sh); }, big_list, &big_n, wtmp);
+      {
+        K lo2;
+        int sh2;
+        uint32_t NB2;
+        uint32_t rank2[kRankPer];
+        bucket_table<KW>(tb, cap_slots, dn2, b.out_keys + base * KW, b.out_counts + base, hist, red_lo, red_hi, wtmp,
+                         nullptr, lo2, sh2, NB2);
+        if (wid > 0)
+          load_and_rank<KW>(b.out_keys + base * KW, b.out_counts + base, dn2, dk, dc, hist, NB2, lo2, sh2, rank2,
+                            nullptr);
+        __syncthreads();
+        if (wid > 0) emit_ranked<KW>(dk, dc, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       }
-      __syncthreads();
-      emit_dense<KW>(dk, dc, dn2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       written += dn2;
       __syncthreads();
     }
@@ -1324,7 +1521,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         }
         ++written;
       }
-      st_release(&b.look[g], kLookIncl | (excl_s + written));
+      st_status(&b.look[g], kLookIncl | (excl_s + written));
     }
     __syncthreads();
     phase(6);
@@ -1338,21 +1535,15 @@ __global__ void k_finish(Buffers b) {
     b.meta->n_distinct = 0;
     return;
   }
-  const unsigned long long v = ld_acquire(&b.look[NF - 1]);
+  const unsigned long long v = ld_status(&b.look[NF - 1]);
   if ((v >> 62) != 2) atomicOr(&b.meta->status, ST_INTERNAL);
   b.meta->n_distinct = v & kLookValue;
 }
 
 // ------------------------------------------------------------------ launches
 static size_t scatter_smem(int kw, int nt, int P1) {
-  const size_t sub = (size_t)nt * 32;
-  return sub * (size_t)(kw * 8) + sub * 2 + (size_t)P1 * 8 + (size_t)P1 * 8;
-}
-// threads per CTA of pass B: the largest of 512/256/128 whose staging fits shared memory
-static int scatter_threads(int kw, int P1, size_t budget) {
-  for (int nt = kw == 1 ? 512 : 256; nt >= 128; nt >>= 1)
-    if (scatter_smem(kw, nt, P1) <= budget) return nt;
-  return 0;
+  const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
+  return sub * (size_t)(kw * 8) + sub * 2 + (size_t)P1 * 12;
 }
 static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 4 + kFineLocalCap * 4 + P1 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
@@ -1374,11 +1565,9 @@ int configure_kernels(int device) {
   }
   KC_SET(k_pack_count<1>);
   KC_SET(k_pack_count<2>);
-  KC_SET((k_scatter<1, 512>));
   KC_SET((k_scatter<1, 256>));
-  KC_SET((k_scatter<1, 128>));
   KC_SET((k_scatter<2, 256>));
-  KC_SET((k_scatter<2, 128>));
+  KC_SET(k_fine_plan);
   KC_SET(k_fine_hist<1>);
   KC_SET(k_fine_hist<2>);
   KC_SET(k_fine_scatter<1>);
@@ -1431,27 +1620,22 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   int launches = 0;
   // partition starts (cstart holds the per-partition counts written by k_col_scan; the
   // scan reads them into shared memory before overwriting)
-  k_bucket_scan<<<1, 1024, (size_t)P1 * 16, st>>>(b.cstart, b.cstart, b.fine_base, b.fine_log2, P1, s.fine_target, nf_max,
-                                                   b.meta);
+  k_bucket_scan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.cstart, P1, b.meta);
   ++launches;
   KC_STEP("k_bucket_scan");
   if (s.n_tiles > 0) {
-    // budget: opt-in shared memory minus the kernel's static part (at most 8.5 KB)
-    const int nt = scatter_threads(s.kw, P1, s.smem_budget - 8704);
-    if (nt == 0) return -(int)cudaErrorInvalidConfiguration;
-    const size_t smB = scatter_smem(s.kw, nt, P1);
+    const size_t smB = scatter_smem(s.kw, 256, P1);
+    if (smB + 8704 > s.smem_budget) return -(int)cudaErrorInvalidConfiguration;
     const unsigned gt = (unsigned)s.n_tiles;
-    if (s.kw == 1) {
-      if (nt == 512) k_scatter<1, 512><<<gt, 512, smB, st>>>(s, b);
-      else if (nt == 256) k_scatter<1, 256><<<gt, 256, smB, st>>>(s, b);
-      else k_scatter<1, 128><<<gt, 128, smB, st>>>(s, b);
-    } else {
-      if (nt == 256) k_scatter<2, 256><<<gt, 256, smB, st>>>(s, b);
-      else k_scatter<2, 128><<<gt, 128, smB, st>>>(s, b);
-    }
+    if (s.kw == 1) k_scatter<1, 256><<<gt, 256, smB, st>>>(s, b);
+    else k_scatter<2, 256><<<gt, 256, smB, st>>>(s, b);
     ++launches;
     KC_STEP("k_scatter");
   }
+  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_log2, P1, s.fine_target, nf_max,
+                                               b.meta);
+  ++launches;
+  KC_STEP("k_fine_plan");
   const unsigned gf = (unsigned)(n_sms * 2);
   if (s.kw == 1) k_fine_hist<1><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);
   else k_fine_hist<2><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);

@@ -125,7 +125,10 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   s.k = k;
   s.canonical = canonical ? 1 : 0;
   s.kw = k <= 32 ? 1 : 2;
-  s.b1 = clog2((L >> 21) + 1) < 10 ? clog2((L >> 21) + 1) : 10;
+  {
+    const int want = clog2((L * (uint64_t)(k <= 32 ? 1 : 2)) / (1u << 20) + 1);
+    s.b1 = want < 11 ? want : 11;
+  }
   const int P1 = 1 << s.b1;
   s.bT_max = kc::table_log2_max(s.kw, ds->smem_optin);
   s.tail = s.bT_max >= 10 ? 1024 : (1 << s.bT_max);
@@ -149,6 +152,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   const size_t o_codes = take(s.n_words * 8), o_inv = take(s.n_words * 4), o_tf = take(s.n_tiles * 8);
   const size_t o_hist = take(s.n_tiles * P1 * 4), o_toff = take(s.n_tiles * P1 * 8);
   const size_t o_cst = take((size_t)(P1 + 1) * 8), o_fb = take((size_t)(P1 + 1) * 4), o_fl = take((size_t)P1);
+  const size_t o_hll = take((size_t)kc::kHllRegs * 4);
   const size_t o_fh = take((size_t)nf_max * 4), o_fo = take((size_t)(nf_max + 1) * 8);
   const size_t o_fc = take((size_t)nf_max * 8), o_look = take((size_t)nf_max * 8);
   const size_t o_kbuf = take(cap * s.kw * 8), o_sbuf = take(cap * s.kw * 8), o_meta = take(sizeof(kc::Meta));
@@ -166,6 +170,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   b.cstart = (uint64_t*)(ws + o_cst);
   b.fine_base = (uint32_t*)(ws + o_fb);
   b.fine_log2 = (uint8_t*)(ws + o_fl);
+  b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);
   b.fcur = (unsigned long long*)(ws + o_fc);
@@ -179,6 +184,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   // the array keeps the previous call's contents: clear what the kernels expect at zero
   if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), strm)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.fhist, 0, (size_t)nf_max * 4, strm)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, strm)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.look, 0, (size_t)nf_max * 8, strm)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.cstart, 0, (size_t)(P1 + 1) * 8, strm)) != cudaSuccess)
     return nfail(KC_ECUDA, std::string("kc_count_noalloc: clearing scratch: ") + cudaGetErrorString(e));
@@ -196,6 +202,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   if (ce != cudaSuccess || se != cudaSuccess)
     return nfail(KC_ECUDA, std::string("kc_count_noalloc: ") + cudaGetErrorString(ce != cudaSuccess ? ce : se));
   if (m.status & kc::ST_BAD_OFFSETS) return nfail(KC_EINVAL, "kc_count_noalloc: offsets must be non-decreasing");
+  if (m.status & kc::ST_PARTITION_OVERFLOW) return nfail(KC_EOVERFLOW, "kc_count_noalloc: a key range holds 2^32 windows");
   if (m.status & kc::ST_COUNT_OVERFLOW) return nfail(KC_EOVERFLOW, "kc_count_noalloc: a count exceeds 2^32 - 1");
   if (m.status & kc::ST_TIMEOUT) return nfail(KC_ETIMEOUT, "kc_count_noalloc: a device-side wait timed out");
   if (m.status & kc::ST_INTERNAL) return nfail(KC_ECUDA, "kc_count_noalloc: internal consistency check failed");
