@@ -249,28 +249,52 @@ __device__ __forceinline__ uint32_t coarse_of(K key, int k, int canonical, int b
   return field32(umap(top32_of(key, k), canonical), 0, b1);
 }
 
-// Windows of one thread: WPT consecutive window ends starting at base q0 = 32j + 32 - ... see
-// win_setup.  With the base stream S aligned so that window i's first base is S's base i,
-// window i's forward key is the top 2k bits of S << 2i and its reverse complement the top
-// 2k bits of R << 2(WPT-1-i), R being the complemented bases in reverse order.  Both
-// shifts are compile-time constants once the loop over i is unrolled.
+// Windows of one thread: WPT consecutive window ends starting at base q0 (q0 = 32j for
+// WPT == 32; q0 = 32j + 16h for WPT == 16).  With the base stream S aligned so that window
+// i's first base is S's base i, window i's forward key is the top 2k bits of S << 2i and
+// its reverse complement the top 2k bits of R << 2(WPT-1-i), R being the complemented
+// bases in reverse order.  Both shifts are compile-time constants once the loop over i is
+// unrolled.  Values are kept top-aligned (key << (64 or 128) - 2k), so the top 32 bits
+// that drive the range map come for free.
 struct Win {
   uint64_t s0, s1, s2;  // S, left-aligned (192 bits; only s0, s1 used for k <= 32)
   uint64_t r0, r1, r2;  // R, left-aligned
   uint64_t m0, m1;      // mask of the top 2k bits (m1 used for k > 32)
-  uint32_t iv, sv;      // invalid / read-start bits of the thread's WPT bases (bit i = base q0 + i)
-  int run;              // valid same-read bases ending at q0 - 1 (capped at 64)
+  uint32_t valid;       // bit i: window i has k bases in ACGTacgt and no read start inside
 };
 
 __device__ __forceinline__ uint64_t shl128_hi(uint64_t a, uint64_t b, int sh) {  // top word of (a:b) << sh, 0 <= sh <= 64
   return sh == 0 ? a : (sh >= 64 ? b : (a << sh) | (b >> (64 - sh)));
 }
 
-// Set up the walk over bases q0 .. q0+WPT-1 of code word j (q0 = 32j + 32 - WPT*(2-h) ... for
-// WPT == 32, q0 = 32j; for WPT == 16, q0 = 32j + 16h).  w2, w1, w0: code words j-2, j-1, j.
+// Mask of valid window ends for the 32 bases of word j: bit e (0..31) is set iff the k
+// bases ending at 32j + e are all bases (inv clear) and no read starts at any of the last
+// k - 1 of them.  inv / starts over words j-2, j-1, j as one 96-bit value, LSB = base 32j-64.
+__device__ __forceinline__ uint32_t valid_mask(uint32_t i2, uint32_t i1, uint32_t i0, uint32_t t2, uint32_t t1,
+                                               uint32_t t0, int k) {
+  const u128 I = (u128)i2 | ((u128)i1 << 32) | ((u128)i0 << 64);
+  const u128 S = (u128)t2 | ((u128)t1 << 32) | ((u128)t0 << 64);
+  // a read start at base p forbids windows holding p-1 and p: mark base p-1 (C = I | S >> 1)
+  // window [e-k+1, e] is valid iff C has no bit in [e-k+1, e-1] and I has no bit at e
+  u128 bad = I;
+  const int w = k - 1;
+  if (w > 0) {
+    const u128 C = I | (S >> 1);
+    u128 Y = C;  // OR over a window of width 2^p ending at each bit
+    int p = 1;
+    while (2 * p <= w) {
+      Y |= Y << p;
+      p *= 2;
+    }
+    if (w > p) Y |= Y << (w - p);  // width w
+    bad |= Y << 1;                 // windows ending at e look at C bits e-1 .. e-w
+  }
+  return ~(uint32_t)(bad >> 64);
+}
+
 template <int KW, int WPT>
-__device__ __forceinline__ void win_setup(uint64_t w2, uint64_t w1, uint64_t w0, uint32_t i2, uint32_t i1, uint32_t i0,
-                                          uint32_t t2, uint32_t t1, uint32_t t0, int h, int k, Win& W) {
+__device__ __forceinline__ void win_setup(uint64_t w2, uint64_t w1, uint64_t w0, uint32_t vmask_word, int h, int k,
+                                          Win& W) {
   // (w2 : w1 : w0) holds bases 32j-64 .. 32j+31; the first window's first base is
   // q0 - k + 1 = 32j + 16h - k + 1, at index 65 + 16h - k of that string.
   const int off = 65 + 16 * h - k;  // base index, >= 1
@@ -302,34 +326,32 @@ __device__ __forceinline__ void win_setup(uint64_t w2, uint64_t w1, uint64_t w0,
     W.m0 = ~0ull;
     W.m1 = k >= 64 ? ~0ull : ~(~0ull >> (2 * k - 64));
   }
-  // run length ending at q0 - 1: the 64 mask bits ending there
-  const int lo = 16 * h;  // bit of q0 - 64 within (i2 | i1 << 32 | i0 << 64)
-  const uint64_t yi = lo == 0 ? ((uint64_t)i2 | ((uint64_t)i1 << 32)) : (((uint64_t)i2 >> 16) | ((uint64_t)i1 << 16) | ((uint64_t)i0 << 48));
-  const uint64_t ys = lo == 0 ? ((uint64_t)t2 | ((uint64_t)t1 << 32)) : (((uint64_t)t2 >> 16) | ((uint64_t)t1 << 16) | ((uint64_t)t0 << 48));
-  W.run = min(__clzll(yi), __clzll(ys) + 1);
-  W.iv = i0 >> lo;
-  W.sv = t0 >> lo;
+  W.valid = vmask_word >> (16 * h);
 }
 
-// Window i of a thread's walk: updates the run length, returns true and the key if valid.
+// Window i: the canonical value, top-aligned (top 64 bits in c0, next 64 in c1 for k > 32).
 template <int KW, int WPT>
-__device__ __forceinline__ bool win_key(Win& W, int i, int k, int canonical, int nvalid, typename KeyT<KW>::T& key) {
-  const int ib = (W.iv >> i) & 1, sb = (W.sv >> i) & 1;
-  W.run = ib ? 0 : (sb ? 1 : min(W.run + 1, 64));
+__device__ __forceinline__ void win_top(const Win& W, int i, int canonical, uint64_t& c0, uint64_t& c1) {
   const int fs = 2 * i, rs = 2 * (WPT - 1 - i);
   if constexpr (KW == 1) {
     const uint64_t f = shl128_hi(W.s0, W.s1, fs) & W.m0;
     const uint64_t r = shl128_hi(W.r0, W.r1, rs) & W.m0;
-    const uint64_t c = (canonical && r < f) ? r : f;
-    key = k >= 32 ? c : c >> (64 - 2 * k);
+    c0 = (canonical && r < f) ? r : f;
+    c1 = 0;
   } else {
     const uint64_t f0 = shl128_hi(W.s0, W.s1, fs), f1 = shl128_hi(W.s1, W.s2, fs) & W.m1;
     const uint64_t r0 = shl128_hi(W.r0, W.r1, rs), r1 = shl128_hi(W.r1, W.r2, rs) & W.m1;
-    const bool rlt = (r0 < f0) || (r0 == f0 && r1 < f1);
-    const u128 c = (canonical && rlt) ? (((u128)r0 << 64) | r1) : (((u128)f0 << 64) | f1);
-    key = k >= 64 ? c : c >> (128 - 2 * k);
+    const bool rlt = canonical && ((r0 < f0) || (r0 == f0 && r1 < f1));
+    c0 = rlt ? r0 : f0;
+    c1 = rlt ? r1 : f1;
   }
-  return i < nvalid && W.run >= k;
+}
+__device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t, int k, uint64_t& key) {
+  key = k >= 32 ? c0 : c0 >> (64 - 2 * k);
+}
+__device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t c1, int k, u128& key) {
+  const u128 c = ((u128)c0 << 64) | c1;
+  key = k >= 64 ? c : c >> (128 - 2 * k);
 }
 
 // ------------------------------------------------------------------ pass A
@@ -381,15 +403,15 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
     __syncthreads();
     if (j < s.n_words) {
       Win W;
-      win_setup<KW, 32>(code_s[t], code_s[t + 1], code, inv_s[t], inv_s[t + 1], inv, st_s[t], st_s[t + 1], st_s[t + 2],
-                        0, s.k, W);
-      const uint64_t left = s.L - j * 32;
-      const int nvalid = left < 32 ? (int)left : 32;
+      const uint32_t vm = valid_mask(inv_s[t], inv_s[t + 1], inv, st_s[t], st_s[t + 1], st_s[t + 2], s.k);
+      win_setup<KW, 32>(code_s[t], code_s[t + 1], code, vm, 0, s.k, W);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        K key;
-        if (win_key<KW, 32>(W, i, s.k, s.canonical, nvalid, key))
-          atomicAdd(&hist_s[coarse_of(key, s.k, s.canonical, s.b1)], 1u);
+        if ((W.valid >> i) & 1u) {
+          uint64_t c0, c1;
+          win_top<KW, 32>(W, i, s.canonical, c0, c1);
+          atomicAdd(&hist_s[field32(umap((uint32_t)(c0 >> 32), s.canonical), 0, s.b1)], 1u);
+        }
       }
     }
   }
@@ -530,10 +552,9 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   constexpr int SUB = NT * WPT;             // windows per sub-step
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
-  K* stage = reinterpret_cast<K*>(sm);                               // [SUB]
-  uint16_t* stage_c = reinterpret_cast<uint16_t*>(stage + SUB);      // [SUB]
-  uint32_t* cursor = reinterpret_cast<uint32_t*>(stage_c + SUB);     // [P1], relative to the partition start
-  uint32_t* hist = cursor + P1;                                      // [P1]
+  K* stage = reinterpret_cast<K*>(sm);                                                // [SUB]
+  unsigned long long* cursor = reinterpret_cast<unsigned long long*>(stage + SUB);   // [P1] absolute write positions
+  uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);                            // [P1]
   uint32_t* soff = hist + P1;                                        // [P1]
   __shared__ uint64_t code_s[NW + 2];
   __shared__ uint32_t inv_s[NW + 2];
@@ -545,7 +566,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   const int wl = t / TPW, h = t % TPW;  // code word of the thread within the sub-step, half
   const uint64_t tile = blockIdx.x;
   for (int c = t; c < P1; c += NT) {
-    cursor[c] = (uint32_t)b.toff[tile * P1 + c];
+    cursor[c] = b.cstart[c] + b.toff[tile * P1 + c];
     hist[c] = 0;
   }
   for (int i = t; i < kHllRegs; i += NT) hll_s[i] = 0;
@@ -585,15 +606,16 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
     if (j < s.n_words) {
       Win W;
       const int sw = wl + 2;
-      win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], inv_s[sw - 2], inv_s[sw - 1], inv_s[sw],
-                         st_s[sw - 2], st_s[sw - 1], st_s[sw], h, s.k, W);
-      const uint64_t q0 = j * 32 + (uint64_t)(WPT == 16 ? 16 * h : 0);
-      const int nvalid = q0 >= s.L ? 0 : (s.L - q0 < (uint64_t)WPT ? (int)(s.L - q0) : WPT);
+      const uint32_t vm = valid_mask(inv_s[sw - 2], inv_s[sw - 1], inv_s[sw], st_s[sw - 2], st_s[sw - 1], st_s[sw], s.k);
+      win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], vm, h, s.k, W);
+      valid = W.valid & (WPT == 32 ? 0xffffffffu : 0xffffu);
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
-        if (win_key<KW, WPT>(W, i, s.k, s.canonical, nvalid, keys[i])) {
-          valid |= 1u << i;
-          const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);
+        if ((valid >> i) & 1u) {
+          uint64_t c0, c1;
+          win_top<KW, WPT>(W, i, s.canonical, c0, c1);
+          top_to_key(c0, c1, s.k, keys[i]);
+          const uint32_t c = field32(umap((uint32_t)(c0 >> 32), s.canonical), 0, s.b1);
           const uint32_t r = atomicAdd(&hist[c], 1u);
           rr[i >> 1] |= r << (16 * (i & 1));
           const uint64_t hh = key_hash(keys[i]);
@@ -612,22 +634,18 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
 #pragma unroll
     for (int i = 0; i < WPT; ++i) {
       if (valid & (1u << i)) {
-        const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);
+        const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
         const uint32_t pos = soff[c] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
         stage[pos] = keys[i];
-        stage_c[pos] = (uint16_t)c;
       }
     }
     __syncthreads();
     const uint32_t n_sub = soff[P1 - 1] + hist[P1 - 1];
     for (uint32_t i = t; i < n_sub; i += NT) {
-      const uint32_t c = stage_c[i];
-      if (c >= (uint32_t)P1) {
-        atomicOr(&b.meta->status, ST_INTERNAL);
-        continue;
-      }
-      const uint64_t pos = b.cstart[c] + cursor[c] + (i - soff[c]);
-      if (pos < s.cap) store_key(b.kbuf, pos, stage[i]);
+      const K key = stage[i];
+      const uint32_t c = coarse_of(key, s.k, s.canonical, s.b1);  // runs are grouped by partition
+      const uint64_t pos = cursor[c] + (i - soff[c]);
+      if (i >= soff[c] && i - soff[c] < hist[c] && pos < s.cap) store_key(b.kbuf, pos, key);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
     __syncthreads();
@@ -660,8 +678,40 @@ __device__ __forceinline__ void load_fine_tables(const Buffers& b, int P1, uint3
 }
 
 constexpr int kFineThreads = 512;
-constexpr int kFinePer = 8;  // keys per thread per chunk
+constexpr int kFinePer = 16;  // keys per thread per chunk (loaded as 16-byte pairs / quads, all before use)
 constexpr int kFineChunk = kFineThreads * kFinePer;
+
+// Load this thread's keys of the chunk [c0, c1): pairs of words (read-only path, all
+// loads issued before any use).  Key m of the thread is chunk key  (m / P) * P * T +
+// threadIdx.x * P + m % P, P = 16 / (8 KW) keys per load, T = threads.
+template <int KW>
+__device__ __forceinline__ void load_chunk(const uint64_t* __restrict__ src, uint64_t c0, uint64_t c1,
+                                           typename KeyT<KW>::T (&keys)[kFinePer], uint32_t& have) {
+  typedef typename KeyT<KW>::T K;
+  constexpr int P = KW == 1 ? 2 : 1;  // keys per 16-byte load
+  have = 0;
+  ulonglong2 v[kFinePer / P];
+#pragma unroll
+  for (int m = 0; m < kFinePer / P; ++m) {
+    const uint64_t i = c0 + (uint64_t)m * P * kFineThreads + (uint64_t)threadIdx.x * P;
+    v[m] = make_ulonglong2(0, 0);
+    if (i + P <= c1) v[m] = __ldg(reinterpret_cast<const ulonglong2*>(src + i * KW));
+    else if (i < c1) v[m].x = __ldg(src + i * KW);  // P == 2 and one key left
+  }
+#pragma unroll
+  for (int m = 0; m < kFinePer / P; ++m) {
+    const uint64_t i = c0 + (uint64_t)m * P * kFineThreads + (uint64_t)threadIdx.x * P;
+    if constexpr (KW == 1) {
+      keys[2 * m] = (K)v[m].x;
+      keys[2 * m + 1] = (K)v[m].y;
+      if (i < c1) have |= 1u << (2 * m);
+      if (i + 1 < c1) have |= 1u << (2 * m + 1);
+    } else {
+      keys[m] = (K)(((u128)v[m].y << 64) | v[m].x);
+      if (i < c1) have |= 1u << m;
+    }
+  }
+}
 
 template <int KW>
 __global__ void __launch_bounds__(kFineThreads) k_fine_hist(Shape s, Buffers b) {
@@ -690,13 +740,13 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_hist(Shape s, Buffers b) 
     __syncthreads();
     const uint32_t g_lo = g_lo_s, span = g_hi_s - g_lo_s;
     const bool local = span <= (uint32_t)kFineLocalCap;
+    K keys[kFinePer];
+    uint32_t have;
+    load_chunk<KW>(b.kbuf, c0, c1, keys, have);
 #pragma unroll
     for (int m = 0; m < kFinePer; ++m) {
-      const uint64_t i = c0 + threadIdx.x + (uint64_t)m * kFineThreads;
-      if (i < c1) {
-        K key;
-        load_key(b.kbuf, i, key);
-        const uint32_t g = fine_index(key, x, fine_base_s, flog_s);
+      if ((have >> m) & 1u) {
+        const uint32_t g = fine_index(keys[m], x, fine_base_s, flog_s);
         if (local && g - g_lo < span) atomicAdd(&lh[g - g_lo], 1u);
         else if (g < s.nf_max) atomicAdd(&b.fhist[g], 1u);
         else atomicOr(&b.meta->status, ST_INTERNAL);
@@ -818,12 +868,12 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers 
     }
     K keys[kFinePer];
     uint32_t gr[kFinePer];
+    uint32_t have;
+    load_chunk<KW>(b.kbuf, c0, c1, keys, have);
 #pragma unroll
     for (int m = 0; m < kFinePer; ++m) {
-      const uint64_t i = c0 + threadIdx.x + (uint64_t)m * kFineThreads;
       gr[m] = 0xffffffffu;
-      if (i < c1) {
-        load_key(b.kbuf, i, keys[m]);
+      if ((have >> m) & 1u) {
         const uint32_t lg = fine_index(keys[m], x, fine_base_s, flog_s) - g_lo;
         if (lg < span) {
           const uint32_t r = atomicAdd(&lh[lg], 1u);
@@ -1074,12 +1124,25 @@ __device__ void table_range(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T*
     red_hi[wid] = mx;
   }
   __syncthreads();
+  if (wid == 0) {  // one warp combines the per-warp results
+    const int nw = (int)(blockDim.x >> 5);
+    mn = lane < nw ? red_lo[lane] : EMPTY;
+    mx = lane < nw ? red_hi[lane] : K(0);
+#pragma unroll
+    for (int dd = 16; dd > 0; dd >>= 1) {
+      const K a = shfl_key(mn, (lane + dd) & 31), c = shfl_key(mx, (lane + dd) & 31);
+      mn = a < mn ? a : mn;
+      mx = c > mx ? c : mx;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      red_lo[0] = mn;
+      red_hi[0] = mx;
+    }
+  }
+  __syncthreads();
   lo = red_lo[0];
   hi = red_hi[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-    lo = red_lo[w] < lo ? red_lo[w] : lo;
-    hi = red_hi[w] > hi ? red_hi[w] : hi;
-  }
 }
 
 // Write the table's entries to stage[0, d) grouped by bucket (key - lo) >> sh, buckets in
@@ -1543,7 +1606,7 @@ __global__ void k_finish(Buffers b) {
 // ------------------------------------------------------------------ launches
 static size_t scatter_smem(int kw, int nt, int P1) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
-  return sub * (size_t)(kw * 8) + sub * 2 + (size_t)P1 * 12;
+  return sub * (size_t)(kw * 8) + (size_t)P1 * 16;
 }
 static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 4 + kFineLocalCap * 4 + P1 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
