@@ -137,6 +137,48 @@ __device__ T block_exclusive_scan(T* data, int n, T* warp_tmp) {
   return total;
 }
 
+// Shared arrays that are scanned by contiguous per-thread chunks are padded (one word per
+// 32) so that those chunks fall in distinct banks.
+__host__ __device__ __forceinline__ uint32_t PAD(uint32_t i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ size_t padded_len(size_t n) { return n + (n >> 5) + 1; }
+
+// block_exclusive_scan over a padded array (logical element i at data[PAD(i)]).
+template <typename T>
+__device__ T block_exclusive_scan_pad(T* data, int n, T* warp_tmp) {
+  const int nt = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = (nt + 31) >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  T s = 0;
+  for (int i = lo; i < hi; ++i) s += data[PAD(i)];
+  T x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_tmp[lane] = w;
+  }
+  __syncthreads();
+  T run = x - s + (wid ? warp_tmp[wid - 1] : 0);
+  const T total = warp_tmp[nw - 1];
+  for (int i = lo; i < hi; ++i) {
+    T v = data[PAD(i)];
+    data[PAD(i)] = run;
+    run += v;
+  }
+  __syncthreads();
+  return total;
+}
+
 // ------------------------------------------------------------------ input checks
 __global__ void k_check_offsets(const uint64_t* offsets, uint64_t n_reads, Meta* meta) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_reads; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -554,8 +596,8 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   const int P1 = 1 << s.b1;
   K* stage = reinterpret_cast<K*>(sm);                                                // [SUB]
   unsigned long long* cursor = reinterpret_cast<unsigned long long*>(stage + SUB);   // [P1] absolute write positions
-  uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);                            // [P1]
-  uint32_t* soff = hist + P1;                                        // [P1]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);                            // [padded P1]
+  uint32_t* soff = hist + padded_len(P1);                                               // [padded P1]
   __shared__ uint64_t code_s[NW + 2];
   __shared__ uint32_t inv_s[NW + 2];
   __shared__ uint32_t st_s[NW + 2];
@@ -567,7 +609,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   const uint64_t tile = blockIdx.x;
   for (int c = t; c < P1; c += NT) {
     cursor[c] = b.cstart[c] + b.toff[tile * P1 + c];
-    hist[c] = 0;
+    hist[PAD(c)] = 0;
   }
   for (int i = t; i < kHllRegs; i += NT) hll_s[i] = 0;
   if (t == 0) rcur_s = b.tile_first[tile];
@@ -616,7 +658,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
           win_top<KW, WPT>(W, i, s.canonical, c0, c1);
           top_to_key(c0, c1, s.k, keys[i]);
           const uint32_t c = field32(umap((uint32_t)(c0 >> 32), s.canonical), 0, s.b1);
-          const uint32_t r = atomicAdd(&hist[c], 1u);
+          const uint32_t r = atomicAdd(&hist[PAD(c)], 1u);
           rr[i >> 1] |= r << (16 * (i & 1));
           const uint64_t hh = key_hash(keys[i]);
           if ((hh >> (64 - kHllSampleLog2)) == 0) {
@@ -628,30 +670,31 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
       }
     }
     __syncthreads();
-    for (int c = t; c < P1; c += NT) soff[c] = hist[c];
+    for (int c = t; c < P1; c += NT) soff[PAD(c)] = hist[PAD(c)];
     __syncthreads();
-    block_exclusive_scan<uint32_t>(soff, P1, wt);
+    block_exclusive_scan_pad<uint32_t>(soff, P1, wt);
 #pragma unroll
     for (int i = 0; i < WPT; ++i) {
       if (valid & (1u << i)) {
         const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
-        const uint32_t pos = soff[c] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+        const uint32_t pos = soff[PAD(c)] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
         stage[pos] = keys[i];
       }
     }
     __syncthreads();
-    const uint32_t n_sub = soff[P1 - 1] + hist[P1 - 1];
+    const uint32_t n_sub = soff[PAD(P1 - 1)] + hist[PAD(P1 - 1)];
     for (uint32_t i = t; i < n_sub; i += NT) {
       const K key = stage[i];
       const uint32_t c = coarse_of(key, s.k, s.canonical, s.b1);  // runs are grouped by partition
-      const uint64_t pos = cursor[c] + (i - soff[c]);
-      if (i >= soff[c] && i - soff[c] < hist[c] && pos < s.cap) store_key(b.kbuf, pos, key);
+      const uint32_t so = soff[PAD(c)];
+      const uint64_t pos = cursor[c] + (i - so);
+      if (i >= so && i - so < hist[PAD(c)] && pos < s.cap) store_key(b.kbuf, pos, key);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
     __syncthreads();
     for (int c = t; c < P1; c += NT) {
-      cursor[c] += hist[c];
-      hist[c] = 0;
+      cursor[c] += hist[PAD(c)];
+      hist[PAD(c)] = 0;
     }
   }
   __syncthreads();
@@ -826,15 +869,15 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers 
   const int P1 = 1 << s.b1;
   K* stage = reinterpret_cast<K*>(sm);                                        // [kFineChunk]
   uint64_t* gbase = reinterpret_cast<uint64_t*>(stage + kFineChunk);          // [kFineLocalCap]
-  uint32_t* lh = reinterpret_cast<uint32_t*>(gbase + kFineLocalCap);          // [kFineLocalCap]
-  uint32_t* soff = lh + kFineLocalCap;                                        // [kFineLocalCap]
-  uint16_t* stage_g = reinterpret_cast<uint16_t*>(soff + kFineLocalCap);      // [kFineChunk]
+  uint32_t* lh = reinterpret_cast<uint32_t*>(gbase + kFineLocalCap);          // [padded kFineLocalCap]
+  uint32_t* soff = lh + padded_len(kFineLocalCap);                            // [padded kFineLocalCap]
+  uint16_t* stage_g = reinterpret_cast<uint16_t*>(soff + padded_len(kFineLocalCap));  // [kFineChunk]
   uint32_t* fine_base_s = reinterpret_cast<uint32_t*>(stage_g + kFineChunk);  // [P1+1]
   uint8_t* flog_s = reinterpret_cast<uint8_t*>(fine_base_s + P1 + 1);         // [P1]
   __shared__ uint32_t g_lo_s, g_hi_s;
   __shared__ uint32_t wt[32];
   load_fine_tables<KW>(b, P1, fine_base_s, flog_s);
-  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
+  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[PAD(i)] = 0;
   const FineCtx x{s.k, s.canonical, s.b1};
   const uint64_t K_total = b.meta->n_windows;
   __syncthreads();
@@ -876,7 +919,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers 
       if ((have >> m) & 1u) {
         const uint32_t lg = fine_index(keys[m], x, fine_base_s, flog_s) - g_lo;
         if (lg < span) {
-          const uint32_t r = atomicAdd(&lh[lg], 1u);
+          const uint32_t r = atomicAdd(&lh[PAD(lg)], 1u);
           gr[m] = (lg << 16) | r;
         } else {
           atomicOr(&b.meta->status, ST_INTERNAL);
@@ -884,37 +927,37 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers 
       }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) soff[i] = lh[i];
+    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) soff[PAD(i)] = lh[PAD(i)];
     __syncthreads();
-    block_exclusive_scan<uint32_t>(soff, (int)span, wt);
+    block_exclusive_scan_pad<uint32_t>(soff, (int)span, wt);
     for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
-      const uint32_t v = lh[i];
+      const uint32_t v = lh[PAD(i)];
       if (v) gbase[i] = g_lo + i < s.nf_max ? atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v) : ~0ull;
     }
 #pragma unroll
     for (int m = 0; m < kFinePer; ++m) {
       if (gr[m] != 0xffffffffu) {
         const uint32_t lg = gr[m] >> 16;
-        const uint32_t pos = soff[lg] + (gr[m] & 0xffffu);
+        const uint32_t pos = soff[PAD(lg)] + (gr[m] & 0xffffu);
         stage[pos] = keys[m];
         stage_g[pos] = (uint16_t)lg;
       }
     }
     __syncthreads();
     // only the keys that were staged (a key outside the chunk's fine range was rejected above)
-    const uint32_t n_staged = soff[span - 1] + lh[span - 1];
+    const uint32_t n_staged = soff[PAD(span - 1)] + lh[PAD(span - 1)];
     for (uint32_t i = threadIdx.x; i < n_staged; i += kFineThreads) {
       const uint32_t lg = stage_g[i];
       if (lg >= span) {
         atomicOr(&b.meta->status, ST_INTERNAL);
         continue;
       }
-      const uint64_t pos = gbase[lg] + (i - soff[lg]);
+      const uint64_t pos = gbase[lg] + (i - soff[PAD(lg)]);
       if (pos < s.cap) store_key(b.sbuf, pos, stage[i]);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) lh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) lh[PAD(i)] = 0;
     __syncthreads();
   }
 }
@@ -972,7 +1015,7 @@ __host__ __device__ constexpr int hist_max(int kw) { return kw == 1 ? 16384 : 81
 
 size_t count_kernel_smem(int kw, int bT_max, int /*unused*/) {
   const size_t slots = (size_t)1 << bT_max;
-  return slots * (size_t)(kw * 8 + 4) + (size_t)hist_max(kw) * 4 + 256;
+  return slots * (size_t)(kw * 8 + 4) + padded_len(hist_max(kw)) * 4 + 256;
 }
 
 int table_log2_max(int kw, size_t smem_optin) {
@@ -1048,7 +1091,7 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
                           typename KeyT<KW>::T hi, int bT, uint32_t* n_new, uint32_t* ovf, uint32_t* special,
                           uint32_t* status) {
   typedef typename KeyT<KW>::T K;
-  constexpr int kIn = KW == 1 ? 4 : 2;  // loads in flight per thread
+  constexpr int kIn = KW == 1 ? 8 : 2;  // loads in flight per thread (u128 keys: register-bound at 64)
   const K EMPTY = all_ones<K>();
   const int lane = threadIdx.x & 31;
   for (uint64_t base = 0; base < n; base += kIn * (uint64_t)blockDim.x) {
@@ -1163,17 +1206,17 @@ __device__ void place_entries(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::
       const K key = tb.keys[s];
       if (key != EMPTY) {
         const uint32_t bk = (uint32_t)((key - lo) >> sh);
-        br[m] = (bk << 16) | atomicAdd(&hist[bk], 1u);  // NB <= 2^14, rank < 2^16
+        br[m] = (bk << 16) | atomicAdd(&hist[PAD(bk)], 1u);  // NB <= 2^14, rank < 2^16
       }
     }
   }
   __syncthreads();
-  block_exclusive_scan<uint32_t>(hist, (int)NB, wtmp);
+  block_exclusive_scan_pad<uint32_t>(hist, (int)NB, wtmp);
 #pragma unroll
   for (int m = 0; m < kSlotsPerThread; ++m) {
     if (br[m] != 0xffffffffu) {
       const uint32_t s = threadIdx.x + m * blockDim.x;
-      const uint32_t pos = hist[br[m] >> 16] + (br[m] & 0xffffu);
+      const uint32_t pos = hist[PAD(br[m] >> 16)] + (br[m] & 0xffffu);
       store_key(stage_keys, pos, tb.keys[s]);
       stage_counts[pos] = tb.counts[s];
     }
@@ -1273,8 +1316,8 @@ __device__ __forceinline__ void load_and_rank(const uint64_t* stage_keys, const 
     const uint32_t bk = base + lane;
     uint32_t a = 0, c = 0;
     if (bk < b_hi) {
-      a = hist[bk];
-      c = (bk + 1 < NB ? hist[bk + 1] : d) - a;
+      a = hist[PAD(bk)];
+      c = (bk + 1 < NB ? hist[PAD(bk + 1)] : d) - a;
     }
     unsigned todo = __ballot_sync(0xffffffffu, c > kBigBucket);
     while (todo) {
@@ -1297,8 +1340,8 @@ __device__ __forceinline__ void load_and_rank(const uint64_t* stage_keys, const 
     if (i < d) {
       const K key = dense_keys[i];
       const uint32_t bk = (uint32_t)((key - lo) >> sh);
-      const uint32_t a = hist[bk];
-      const uint32_t e = bk + 1 < NB ? hist[bk + 1] : d;
+      const uint32_t a = hist[PAD(bk)];
+      const uint32_t e = bk + 1 < NB ? hist[PAD(bk + 1)] : d;
       uint32_t r = a;
       if (e - a > kBigBucket) {
         r = i;
@@ -1345,7 +1388,7 @@ __device__ void bucket_table(Table<KW> tb, uint32_t nslots, uint32_t d, uint64_t
   while (NB < (uint32_t)hist_max(KW) && NB < 2 * d) NB <<= 1;  // at most two entries per bucket on average
   const int bB = 31 - __clz(NB);
   sh = d == 0 ? 0 : max(0, bitlen(K(hi - lo)) - bB);
-  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[i] = 0;
+  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[PAD(i)] = 0;
   __syncthreads();
   if (prof && threadIdx.x == 0) {
     const long long now = clock64();
@@ -1606,11 +1649,12 @@ __global__ void k_finish(Buffers b) {
 // ------------------------------------------------------------------ launches
 static size_t scatter_smem(int kw, int nt, int P1) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
-  return sub * (size_t)(kw * 8) + (size_t)P1 * 16;
+  return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4;
 }
 static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 4 + kFineLocalCap * 4 + P1 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
-  return (size_t)kFineChunk * (kw * 8) + kFineLocalCap * (8 + 4 + 4) + kFineChunk * 2 + (size_t)(P1 + 1) * 4 + P1 + 16;
+  return (size_t)kFineChunk * (kw * 8) + kFineLocalCap * 8 + 2 * padded_len(kFineLocalCap) * 4 + kFineChunk * 2 +
+         (size_t)(P1 + 1) * 4 + P1 + 16;
 }
 
 int configure_kernels(int device) {
