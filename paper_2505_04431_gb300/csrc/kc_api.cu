@@ -310,6 +310,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   const size_t o_hll = lay.add((size_t)kc::kHllRegs * 4);
   const size_t o_fh = lay.add((size_t)nf_max * 4);
   const size_t o_fo = lay.add((size_t)(nf_max + 1) * 8);
+  const size_t o_flo = lay.add((size_t)(nf_max + 1) * 4);
   const size_t o_fc = lay.add((size_t)nf_max * 8);
   const size_t o_look = lay.add((size_t)nf_max * 8);
   const size_t o_kbuf = lay.add(s.cap * s.kw * 8);
@@ -349,6 +350,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);
+  b.flo = (uint32_t*)(ws + o_flo);
   b.fcur = (unsigned long long*)(ws + o_fc);
   b.look = (unsigned long long*)(ws + o_look);
   b.kbuf = (uint64_t*)(ws + o_kbuf);

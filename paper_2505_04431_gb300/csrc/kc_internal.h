@@ -88,6 +88,7 @@ struct Buffers {
   uint32_t* hll;          // [kHllRegs] distinct-key sketch (max-merged by pass B)
   uint32_t* fhist;        // [nf_max] keys per fine partition
   uint64_t* foff;         // [nf_max + 1] fine partition starts
+  uint32_t* flo;          // [nf_max + 1] first range-map value u of each fine partition (0 after the last)
   unsigned long long* fcur;  // [nf_max] fine scatter cursors
   unsigned long long* look;  // [nf_max] look-back status words
   uint64_t* kbuf;

@@ -68,6 +68,18 @@ __device__ __forceinline__ u128 shfl_key(u128 v, int src) {
 
 // Look-back status words carry their own payload (flag and value in one 64-bit word) and
 // guard no other data, so relaxed GPU-scope accesses are enough.
+// Asynchronous 4- and 8-byte copies from global to shared memory (cp.async); the issuing
+// thread waits for all of its copies with cp_async_wait_all.
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -289,6 +301,57 @@ __device__ __forceinline__ uint32_t field32(uint32_t u, int skip, int bits) {
 template <class K>
 __device__ __forceinline__ uint32_t coarse_of(K key, int k, int canonical, int b1) {
   return field32(umap(top32_of(key, k), canonical), 0, b1);
+}
+
+// floor(sqrt(v)) from 32-bit conversions and single-precision arithmetic (64-bit
+// conversions and double precision are slow on this GPU): the single-precision root is
+// within 2^32 * 2^-24 of the true one; one Newton step on the exact residual brings it
+// within a few units, and exact integer comparisons finish.  The root is below 2^32, so
+// every square fits in 64 bits.
+__host__ __device__ __forceinline__ float u64_to_float(uint64_t v) {
+  return (float)(uint32_t)(v >> 32) * 4294967296.0f + (float)(uint32_t)v;
+}
+__host__ __device__ __forceinline__ uint64_t isqrt64(uint64_t v) {
+  const float f = sqrtf(u64_to_float(v));
+  uint64_t y = f >= 4294967296.0f ? 0xffffffffull : (uint64_t)(uint32_t)f;
+  if (y > 0) {
+    const int64_t r = (int64_t)(v - y * y);  // |r| < 2^42
+    const float rf = (float)(int32_t)(r >> 32) * 4294967296.0f + (float)(uint32_t)r;
+    const int64_t z = (int64_t)y + (int32_t)(rf / (2.0f * (float)(uint32_t)y));  // step below 2^10
+    y = z < 0 ? 0 : (z > 0xffffffffll ? 0xffffffffull : (uint64_t)z);
+  }
+  while (y > 0 && y * y > v) --y;
+  while (y < 0xffffffffull && (y + 1) * (y + 1) <= v) ++y;
+  return y;
+}
+
+// The top-32-bit values x whose range-map value lies in [ulo, uhi]: [xlo, xhi] (empty when
+// xlo > xhi).  Canonical: umap(x) = 2^32 - 1 - floor(y^2 / 2^32) with y = 2^32 - 1 - x, so
+// umap(x) >= ulo  <=>  y^2 < (2^32 - ulo) 2^32   and   umap(x) <= uhi  <=>  y^2 >= (2^32 - 1 - uhi) 2^32.
+__host__ __device__ __forceinline__ void x_range(uint32_t ulo, uint32_t uhi, int canonical, uint32_t& xlo,
+                                                 uint32_t& xhi) {
+  if (!canonical) {
+    xlo = ulo;
+    xhi = uhi;
+    return;
+  }
+  const uint64_t ymax = isqrt64(((uint64_t)(0x100000000ull - ulo) << 32) - 1);  // wraps to 2^64 - 1 for ulo = 0
+  xlo = 0xffffffffu - (uint32_t)(ymax < 0xffffffffull ? ymax : 0xffffffffull);
+  const uint64_t m = (uint64_t)(~uhi) << 32;
+  const uint64_t ymin = m == 0 ? 0 : isqrt64(m - 1) + 1;  // ceil(sqrt(m))
+  xhi = ymin > 0xffffffffull ? 0u : 0xffffffffu - (uint32_t)ymin;
+  if (ymin > 0xffffffffull) xlo = 1;  // no x maps at or below uhi (only uhi = 0): empty
+}
+
+// Keys (2k bits) whose top 32 bits lie in [xlo, xhi].
+__host__ __device__ __forceinline__ void key_range(uint32_t xlo, uint32_t xhi, int k, uint64_t& lo, uint64_t& hi) {
+  lo = ((uint64_t)xlo << 32) >> (64 - 2 * k);
+  hi = (((uint64_t)xhi << 32) | 0xffffffffull) >> (64 - 2 * k);
+}
+__host__ __device__ __forceinline__ void key_range(uint32_t xlo, uint32_t xhi, int k, u128& lo, u128& hi) {
+  const int sh = 2 * k - 32;
+  lo = (u128)xlo << sh;
+  hi = ((u128)xhi << sh) | (((u128)1 << sh) - 1);
 }
 
 // Windows of one thread: WPT consecutive window ends starting at base q0 (q0 = 32j for
@@ -514,8 +577,8 @@ __global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, 
 // Fine split of every coarse partition, after pass B: the distinct-key estimate (a sampled
 // HyperLogLog filled by pass B) gives the duplication factor K / D, and a fine partition
 // aims at fine_target distinct keys, i.e. fine_target * K / D keys.  One block.
-__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint8_t* fine_log2, int P1,
-                            uint32_t fine_target, uint32_t nf_max, Meta* meta) {
+__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint8_t* fine_log2,
+                            uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
   extern __shared__ uint64_t fsc[];  // [P1]
   __shared__ uint64_t wt[32];
   __shared__ float zsum_s[32], zeros_s[32];
@@ -566,8 +629,16 @@ __global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_
   }
   __syncthreads();
   const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1, wt);
-  for (int c = threadIdx.x; c < P1; c += blockDim.x) fine_base[c] = (uint32_t)fsc[c];
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) {
+    fine_base[c] = (uint32_t)fsc[c];
+    // fine partition fine_base[c] + f holds the values u with coarse field c and fine field f
+    const int bf = fine_log2[c];
+    const uint32_t u0 = (uint32_t)((uint64_t)c << (32 - b1));
+    for (uint32_t f = 0; f < (1u << bf); ++f)
+      if (fsc[c] + f < nf_max) flo[fsc[c] + f] = u0 | (uint32_t)((uint64_t)f << (32 - b1 - bf));
+  }
   if (threadIdx.x == 0) {
+    if (NF <= nf_max) flo[NF] = 0;  // so that the last partition ends at u = 2^32 - 1
     fine_base[P1] = (uint32_t)NF;
     meta->n_fine = NF <= nf_max ? NF : 0;  // later kernels never index past nf_max
     if (NF > nf_max) atomicOr(&meta->status, ST_INTERNAL);
@@ -1007,15 +1078,15 @@ struct Table {
   uint32_t* counts;
 };
 
-// Count kernel shared memory: a hash table of 2^bT_max slots (key + count) and a bucket
-// histogram of kHistMax(kw) entries.  After the count, the table's bytes hold the dense
-// array of distinct keys (at most 3/4 of the slots).
+// Count kernel shared memory: a hash table of 2^bT_max slots (key + count), a bucket
+// histogram of hist_max(kw) entries and the 16-bit slot numbers of up to 3/4 of the slots
+// in output order.
 constexpr int kTableLog2Cap = 13;  // 8192 slots: 8 per thread of the 1024-thread block
 __host__ __device__ constexpr int hist_max(int kw) { return kw == 1 ? 16384 : 8192; }
 
 size_t count_kernel_smem(int kw, int bT_max, int /*unused*/) {
   const size_t slots = (size_t)1 << bT_max;
-  return slots * (size_t)(kw * 8 + 4) + padded_len(hist_max(kw)) * 4 + 256;
+  return slots * (size_t)(kw * 8 + 4) + padded_len(hist_max(kw)) * 4 + ((3 * slots) >> 2) * 2 + 256;
 }
 
 int table_log2_max(int kw, size_t smem_optin) {
@@ -1044,7 +1115,7 @@ __device__ __forceinline__ void bar_workers() { asm volatile("bar.sync 1, %0;" :
 // was found within the probe limit.
 template <int KW>
 __device__ __forceinline__ bool count_insert(Table<KW> tb, typename KeyT<KW>::T key, uint32_t inc, int bT,
-                                             uint32_t* n_new, uint32_t* status) {
+                                             uint32_t* n_new, bool check, uint32_t* status) {
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
   const uint32_t mask = (1u << bT) - 1;
@@ -1067,8 +1138,12 @@ __device__ __forceinline__ bool count_insert(Table<KW> tb, typename KeyT<KW>::T 
       hit = (old == EMPTY || old == key);
     }
     if (hit) {
-      const uint32_t o = atomicAdd(&tb.counts[s], inc);
-      if (o > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
+      if (check) {
+        const uint32_t o = atomicAdd(&tb.counts[s], inc);
+        if (o > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
+      } else {
+        atomicAdd(&tb.counts[s], inc);  // result unused: a reduction
+      }
       return true;
     }
   }
@@ -1094,6 +1169,7 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
   constexpr int kIn = KW == 1 ? 8 : 2;  // loads in flight per thread (u128 keys: register-bound at 64)
   const K EMPTY = all_ones<K>();
   const int lane = threadIdx.x & 31;
+  const bool check = n > 0xffffffffull;  // a count can pass 2^32 - 1 only in a partition that large
   for (uint64_t base = 0; base < n; base += kIn * (uint64_t)blockDim.x) {
     K kk[kIn];
     bool aa[kIn];
@@ -1119,14 +1195,14 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
           const uint32_t inc = __popc(am);
           if (k0 == EMPTY) {
             if (atomicAdd(special, inc) > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
-          } else if (!count_insert<KW>(tb, k0, inc, bT, n_new, status)) {
+          } else if (!count_insert<KW>(tb, k0, inc, bT, n_new, check, status)) {
             atomicOr(ovf, 1u);
           }
         }
       } else if (act) {
         if (key == EMPTY) {
           if (atomicAdd(special, 1u) == 0xffffffffu) atomicOr(status, ST_COUNT_OVERFLOW);
-        } else if (!count_insert<KW>(tb, key, 1u, bT, n_new, status)) {
+        } else if (!count_insert<KW>(tb, key, 1u, bT, n_new, check, status)) {
           atomicOr(ovf, 1u);
         }
       }
@@ -1141,21 +1217,11 @@ template <> __device__ __forceinline__ int bitlen(u128 v) {
   return hi ? 128 - __clzll(hi) : 64 - __clzll((uint64_t)v);
 }
 
-// Smallest and largest key in the table (all threads; the result is returned to all).
-template <int KW>
-__device__ void table_range(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T* red_lo, typename KeyT<KW>::T* red_hi,
-                            typename KeyT<KW>::T& lo, typename KeyT<KW>::T& hi) {
-  typedef typename KeyT<KW>::T K;
-  const K EMPTY = all_ones<K>();
+// Block-wide min of mn and max of mx (all threads; the result is returned to all).
+template <class K>
+__device__ void block_range(K mn, K mx, K* red_lo, K* red_hi, K& lo, K& hi) {
+  const K EMPTY = ~(K)0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  K mn = EMPTY, mx = 0;
-  for (uint32_t s = threadIdx.x; s < nslots; s += blockDim.x) {
-    const K key = tb.keys[s];
-    if (key != EMPTY) {
-      mn = key < mn ? key : mn;
-      mx = key > mx ? key : mx;
-    }
-  }
 #pragma unroll
   for (int dd = 16; dd > 0; dd >>= 1) {
     const K a = shfl_key(mn, (lane + dd) & 31), c = shfl_key(mx, (lane + dd) & 31);
@@ -1188,46 +1254,10 @@ __device__ void table_range(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T*
   hi = red_hi[0];
 }
 
-// Write the table's entries to stage[0, d) grouped by bucket (key - lo) >> sh, buckets in
-// ascending order (an ordered counting sort; entries inside a bucket are unordered).
-// hist[0, NB) must be zero on entry; on return it holds each bucket's first position.
-// All threads; nslots <= kSlotsPerThread * blockDim.x.
-template <int KW>
-__device__ void place_entries(Table<KW> tb, uint32_t nslots, typename KeyT<KW>::T lo, int sh, uint32_t* hist,
-                              uint32_t NB, uint64_t* stage_keys, uint32_t* stage_counts, uint32_t* wtmp) {
-  typedef typename KeyT<KW>::T K;
-  const K EMPTY = all_ones<K>();
-  uint32_t br[kSlotsPerThread];
-#pragma unroll
-  for (int m = 0; m < kSlotsPerThread; ++m) {
-    const uint32_t s = threadIdx.x + m * blockDim.x;
-    br[m] = 0xffffffffu;
-    if (s < nslots) {
-      const K key = tb.keys[s];
-      if (key != EMPTY) {
-        const uint32_t bk = (uint32_t)((key - lo) >> sh);
-        br[m] = (bk << 16) | atomicAdd(&hist[PAD(bk)], 1u);  // NB <= 2^14, rank < 2^16
-      }
-    }
-  }
-  __syncthreads();
-  block_exclusive_scan_pad<uint32_t>(hist, (int)NB, wtmp);
-#pragma unroll
-  for (int m = 0; m < kSlotsPerThread; ++m) {
-    if (br[m] != 0xffffffffu) {
-      const uint32_t s = threadIdx.x + m * blockDim.x;
-      const uint32_t pos = hist[PAD(br[m] >> 16)] + (br[m] & 0xffffu);
-      store_key(stage_keys, pos, tb.keys[s]);
-      stage_counts[pos] = tb.counts[s];
-    }
-  }
-  __syncthreads();
-}
-
-// Sort keys[a, a+c) (with their counts) by one warp: a bitonic network whose comparators
-// all put the smaller key first, so positions past c act as +infinity and are skipped.
+// Sort idx[a, a+c) by the keys the slots hold, by one warp: a bitonic network whose
+// comparators all put the smaller key first, so positions past c act as +infinity.
 template <class K>
-__device__ void warp_sort_segment(K* keys, uint32_t* counts, uint32_t a, uint32_t c) {
+__device__ void warp_sort_idx(const K* keys, uint16_t* idx, uint32_t a, uint32_t c) {
   const int lane = threadIdx.x & 31;
   uint32_t M = 1;
   while (M < c) M <<= 1;
@@ -1236,13 +1266,10 @@ __device__ void warp_sort_segment(K* keys, uint32_t* counts, uint32_t a, uint32_
       for (uint32_t i = lane; i < M; i += 32) {
         const uint32_t j = (stride == (size >> 1)) ? (i ^ (size - 1)) : (i ^ stride);
         if (j > i && j < c) {
-          const K x = keys[a + i], y = keys[a + j];
-          if (y < x) {
-            keys[a + i] = y;
-            keys[a + j] = x;
-            const uint32_t cx = counts[a + i];
-            counts[a + i] = counts[a + j];
-            counts[a + j] = cx;
+          const uint16_t x = idx[a + i], y = idx[a + j];
+          if (keys[y] < keys[x]) {
+            idx[a + i] = y;
+            idx[a + j] = x;
           }
         }
       }
@@ -1251,114 +1278,135 @@ __device__ void warp_sort_segment(K* keys, uint32_t* counts, uint32_t a, uint32_
   }
 }
 
-__device__ __forceinline__ uint64_t shfl_xor_key(uint64_t v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
-__device__ __forceinline__ u128 shfl_xor_key(u128 v, int m) {
-  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, m);
-  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), m);
-  return ((u128)hi << 64) | lo;
+constexpr int kRankPer = 7;           // positions per worker thread: 7 * 992 >= 3/4 of 8192 slots
+constexpr int kRankRegs = (kRankPer + 1) / 2;  // ranks (< 2^13) are kept two per register
+__device__ __forceinline__ uint32_t rank_get(const uint32_t (&rk)[kRankRegs], int m) {
+  return (rk[m >> 1] >> (16 * (m & 1))) & 0xffffu;
 }
+constexpr uint32_t kBigBucket = 256;  // buckets above this are sorted by a warp, not ranked by counting
 
-// Sort keys[a, a+c), c <= 32, with their counts: one entry per lane, a bitonic network on
-// shuffles (lanes past c hold the largest key and stay at the end).  Whole warp calls it.
-template <class K>
-__device__ __forceinline__ void warp_sort32(K* keys, uint32_t* counts, uint32_t a, uint32_t c) {
-  const int lane = threadIdx.x & 31;
-  const bool have = (uint32_t)lane < c;
-  K key = have ? keys[a + lane] : ~(K)0;
-  uint32_t cnt = have ? counts[a + lane] : 0u;
+constexpr int kBigMax = 32;  // more than d / kBigBucket <= 6144 / 257
+
+// Order the table's d occupied slots for output (all threads).  The key range [lo, hi]
+// of the table is read from range_s[0..1] (written by one thread before the call).  NB
+// buckets (key - lo) >> sh, one to two per key; an ordered counting sort of the slot
+// numbers into idx[0, d), bucket by bucket (buckets ascending, slots unordered inside a
+// bucket); hist[PAD(b)] is left holding bucket b's first position, and big_s[0, *big_n)
+// lists the buckets above kBigBucket entries.
+template <int KW>
+__device__ void bucket_slots(Table<KW> tb, uint32_t nslots, uint32_t d, const typename KeyT<KW>::T* range_s,
+                             uint32_t* hist, uint16_t* idx, uint32_t* wtmp, uint32_t* big_s, uint32_t* big_n,
+                             typename KeyT<KW>::T& lo, int& sh, uint32_t& NB, uint32_t* status,
+                             unsigned long long* prof = nullptr) {
+  typedef typename KeyT<KW>::T K;
+  const K EMPTY = all_ones<K>();
+  long long tm = clock64();
+  auto mark = [&](int i) {
+    if (prof && threadIdx.x == 0) {
+      const long long now = clock64();
+      atomicAdd(&prof[i], (unsigned long long)(now - tm));
+      tm = now;
+    }
+  };
+  NB = 1;
+  while (NB < (uint32_t)hist_max(KW) && NB < d) NB <<= 1;
+  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[PAD(i)] = 0;
+  if (threadIdx.x == 0) *big_n = 0;
+  __syncthreads();
+  mark(2);
+  lo = range_s[0];
+  const K hi = range_s[1];
+  const int bB = 31 - __clz(NB);
+  sh = d == 0 ? 0 : max(0, bitlen(K(hi - lo)) - bB);
+  uint32_t br[kSlotsPerThread];
 #pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      const K other = shfl_xor_key(key, j);
-      const uint32_t oc = __shfl_xor_sync(0xffffffffu, cnt, j);
-      const bool up = (lane & size) == 0, lower = (lane & j) == 0;
-      const bool take = (lower == up) ? (other < key) : (key < other);
-      if (take) {
-        key = other;
-        cnt = oc;
+  for (int m = 0; m < kSlotsPerThread; ++m) {
+    const uint32_t s = threadIdx.x + m * blockDim.x;
+    br[m] = 0xffffffffu;
+    if (s < nslots) {
+      const K key = tb.keys[s];
+      if (key != EMPTY) {
+        if (key < lo || key > hi) {  // cannot happen: the range holds every key of the table
+          atomicOr(status, ST_INTERNAL);
+        } else {
+          const uint32_t bk = (uint32_t)((key - lo) >> sh);
+          const uint32_t r = atomicAdd(&hist[PAD(bk)], 1u);
+          br[m] = (bk << 16) | r;  // NB <= 2^14, rank < 2^16
+          if (r == kBigBucket) {   // the entry that takes bucket bk past kBigBucket
+            const uint32_t q = atomicAdd(big_n, 1u);
+            if (q < kBigMax) big_s[q] = bk;
+            else atomicOr(status, ST_INTERNAL);
+          }
+        }
       }
     }
   }
-  if (have) {
-    keys[a + lane] = key;
-    counts[a + lane] = cnt;
-  }
+  __syncthreads();
+  mark(5);
+  block_exclusive_scan_pad<uint32_t>(hist, (int)NB, wtmp);
+  mark(6);
+#pragma unroll
+  for (int m = 0; m < kSlotsPerThread; ++m)
+    if (br[m] != 0xffffffffu) idx[hist[PAD(br[m] >> 16)] + (br[m] & 0xffffu)] = (uint16_t)(threadIdx.x + m * blockDim.x);
+  __syncthreads();
+  mark(7);
 }
 
-constexpr int kRankPer = 7;        // entries per worker thread: 7 * 992 >= 3/4 of 8192 slots
-constexpr uint32_t kBigBucket = 256;  // buckets above this are sorted in place by a warp first
-
-// Worker warps: read the bucket-grouped staged entries into the dense shared arrays, then
-// give every entry its rank inside the partition: its bucket's first position plus the
-// number of smaller keys in the same bucket (buckets are small; the rare bucket above
-// kBigBucket entries is sorted in place by one warp and ranked by position).
+// Worker warps: the rank of the entry at each bucket-grouped position j (its bucket's
+// first position plus the number of smaller keys in the bucket).  The rare bucket above
+// kBigBucket entries is first sorted in place by one warp and ranked by position.
 template <int KW>
-__device__ __forceinline__ void load_and_rank(const uint64_t* stage_keys, const uint32_t* stage_counts, uint32_t d,
-                                              typename KeyT<KW>::T* dense_keys, uint32_t* dense_counts,
-                                              const uint32_t* hist, uint32_t NB, typename KeyT<KW>::T lo, int sh,
-                                              uint32_t (&rank)[kRankPer], unsigned long long* prof) {
+__device__ __forceinline__ void rank_slots(Table<KW> tb, const uint16_t* idx_c, uint16_t* idx, uint32_t d,
+                                           const uint32_t* hist, uint32_t NB, typename KeyT<KW>::T lo, int sh,
+                                           const uint32_t* big_s, uint32_t n_big, uint32_t (&rank)[kRankRegs],
+                                           unsigned long long* prof) {
   typedef typename KeyT<KW>::T K;
-  const int t = threadIdx.x - 32, wid = t >> 5, lane = t & 31;
+  const int t = threadIdx.x - 32, wid = t >> 5;
   long long tm = clock64();
-  for (uint32_t i = t; i < d; i += kWorkers) {
-    K key;
-    load_key(stage_keys, i, key);
-    dense_keys[i] = key;
-    dense_counts[i] = stage_counts[i];
-  }
-  bar_workers();
-  // rare large buckets: one warp each, in place (each warp scans a slice of the buckets)
   constexpr int kWarps = kWorkers / 32;
-  const uint32_t per = (NB + kWarps - 1) / kWarps;
-  const uint32_t b_lo = min(NB, (uint32_t)wid * per), b_hi = min(NB, b_lo + per);
-  for (uint32_t base = b_lo; base < b_hi; base += 32) {
-    const uint32_t bk = base + lane;
-    uint32_t a = 0, c = 0;
-    if (bk < b_hi) {
-      a = hist[PAD(bk)];
-      c = (bk + 1 < NB ? hist[PAD(bk + 1)] : d) - a;
+  if (n_big) {  // rare: one warp per big bucket
+    for (uint32_t q = wid; q < min(n_big, (uint32_t)kBigMax); q += kWarps) {
+      const uint32_t bk = big_s[q];
+      const uint32_t a = hist[PAD(bk)];
+      const uint32_t e = bk + 1 < NB ? hist[PAD(bk + 1)] : d;
+      warp_sort_idx<K>(tb.keys, idx, a, e - a);
     }
-    unsigned todo = __ballot_sync(0xffffffffu, c > kBigBucket);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      warp_sort_segment<K>(dense_keys, dense_counts, __shfl_sync(0xffffffffu, a, src),
-                           __shfl_sync(0xffffffffu, c, src));
-    }
+    bar_workers();
   }
-  bar_workers();
   if (prof && t == 0) {
     const long long now = clock64();
     atomicAdd(&prof[3], (unsigned long long)(now - tm));
     tm = now;
   }
 #pragma unroll
+  for (int m = 0; m < kRankRegs; ++m) rank[m] = 0xffffffffu;
+#pragma unroll
   for (int m = 0; m < kRankPer; ++m) {
-    const uint32_t i = t + m * kWorkers;
-    rank[m] = 0xffffffffu;
-    if (i < d) {
-      const K key = dense_keys[i];
+    const uint32_t j = t + m * kWorkers;
+    if (j < d) {
+      const K key = tb.keys[idx_c[j]];
       const uint32_t bk = (uint32_t)((key - lo) >> sh);
       const uint32_t a = hist[PAD(bk)];
       const uint32_t e = bk + 1 < NB ? hist[PAD(bk + 1)] : d;
       uint32_t r = a;
       if (e - a > kBigBucket) {
-        r = i;
+        r = j;
       } else {
-        for (uint32_t j = a; j < e; ++j) r += dense_keys[j] < key;
+        for (uint32_t q = a; q < e; ++q) r += tb.keys[idx_c[q]] < key;
       }
-      rank[m] = r;
+      const int sh = 16 * (m & 1);
+      rank[m >> 1] = (rank[m >> 1] & ~(0xffffu << sh)) | (r << sh);
     }
   }
   if (prof && t == 0) atomicAdd(&prof[4], (unsigned long long)(clock64() - tm));
 }
 
-// Worker threads: write their entries at out[base + rank].
+// Worker threads: write the entry at each grouped position j to out[base + rank].  Ranks
+// differ from j by less than a bucket, so the writes of a warp are nearly contiguous.
 template <int KW>
-__device__ __forceinline__ void emit_ranked(const typename KeyT<KW>::T* dense_keys, const uint32_t* dense_counts,
-                                            uint32_t d, const uint32_t (&rank)[kRankPer], uint64_t base,
-                                            uint64_t* out_keys, uint32_t* out_counts, uint64_t cap, uint32_t* status) {
+__device__ __forceinline__ void emit_slots(Table<KW> tb, const uint16_t* idx, uint32_t d,
+                                           const uint32_t (&rank)[kRankRegs], uint64_t base, uint64_t* out_keys,
+                                           uint32_t* out_counts, uint64_t cap, uint32_t* status) {
   const int t = threadIdx.x - 32;
   if (base + d > cap) {
     if (t == 0) atomicOr(status, ST_INTERNAL);
@@ -1366,37 +1414,14 @@ __device__ __forceinline__ void emit_ranked(const typename KeyT<KW>::T* dense_ke
   }
 #pragma unroll
   for (int m = 0; m < kRankPer; ++m) {
-    const uint32_t i = t + m * kWorkers;
-    if (i < d && rank[m] < d) {
-      store_key(out_keys, base + rank[m], dense_keys[i]);
-      out_counts[base + rank[m]] = dense_counts[i];
+    const uint32_t j = t + m * kWorkers;
+    const uint32_t r = rank_get(rank, m);
+    if (j < d && r < d) {
+      const uint32_t s = idx[j];
+      store_key(out_keys, base + r, tb.keys[s]);
+      out_counts[base + r] = tb.counts[s];
     }
   }
-}
-
-// Key range of the current table and an ordered counting sort of its entries into NB
-// buckets, written to `stage` (global) grouped by bucket.  All threads.
-template <int KW>
-__device__ void bucket_table(Table<KW> tb, uint32_t nslots, uint32_t d, uint64_t* stage_keys, uint32_t* stage_counts,
-                             uint32_t* hist, typename KeyT<KW>::T* red_lo, typename KeyT<KW>::T* red_hi, uint32_t* wtmp,
-                             unsigned long long* prof, typename KeyT<KW>::T& lo, int& sh, uint32_t& NB) {
-  typedef typename KeyT<KW>::T K;
-  long long tm = clock64();
-  K hi;
-  table_range<KW>(tb, nslots, red_lo, red_hi, lo, hi);
-  NB = 1;
-  while (NB < (uint32_t)hist_max(KW) && NB < 2 * d) NB <<= 1;  // at most two entries per bucket on average
-  const int bB = 31 - __clz(NB);
-  sh = d == 0 ? 0 : max(0, bitlen(K(hi - lo)) - bB);
-  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[PAD(i)] = 0;
-  __syncthreads();
-  if (prof && threadIdx.x == 0) {
-    const long long now = clock64();
-    atomicAdd(&prof[0], (unsigned long long)(now - tm));
-    tm = now;
-  }
-  place_entries<KW>(tb, nslots, lo, sh, hist, NB, stage_keys, stage_counts, wtmp);
-  if (prof && threadIdx.x == 0) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
 }
 
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
@@ -1406,18 +1431,23 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const uint32_t cap_slots = 1u << s.bT_max;
+  const uint32_t dcap = (3u * cap_slots) >> 2;  // most distinct keys a table is ordered with
   uint32_t* hist = reinterpret_cast<uint32_t*>(sm + (size_t)cap_slots * (KW * 8 + 4));
-  __shared__ uint64_t g_s, excl_s;
+  uint16_t* idx = reinterpret_cast<uint16_t*>(hist + padded_len(hist_max(KW)));  // [dcap]
+  __shared__ uint64_t excl_s, next_s[3];  // next ticket, its input range
+  __shared__ uint32_t next_u[2];          // its range-map interval: [next_u[0], next_u[1] - 1]
   __shared__ uint32_t ovf_s, special_s, nnew_s;
   __shared__ uint32_t wtmp[32];
   __shared__ K red_lo[32], red_hi[32];
   __shared__ K stk_lo[160], stk_hi[160];
+  __shared__ K range_s[2];
+  __shared__ uint32_t big_s[kBigMax], big_n;
   __shared__ int stk_n;
   const K EMPTY = all_ones<K>();
   const uint64_t NF = b.meta->n_fine;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* stage_cnt_all = reinterpret_cast<uint32_t*>(b.kbuf);  // kbuf is free once the fine split is done
   unsigned long long* prof = s.profile ? reinterpret_cast<unsigned long long*>(b.meta->sub_cycles) : nullptr;
+  unsigned long long* ticket = reinterpret_cast<unsigned long long*>(&b.meta->ticket);
   // profiled plans: thread 0 adds the cycles spent in each phase (0 clear, 1 count, 2 -,
   // 3 order, 4 look-back (warp 0, overlapped), 5 emit, 6 overflow path, 7 ticket + setup)
   long long t_mark = clock64();
@@ -1428,22 +1458,35 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       t_mark = now;
     }
   };
-  // dense arrays reuse the table bytes: at most 3/4 of the slots
-  const uint32_t dcap = (3u * cap_slots) >> 2;
-  K* dk = reinterpret_cast<K*>(sm);
-  uint32_t* dc = reinterpret_cast<uint32_t*>(dk + dcap);
+  // The next partition's ticket, input range and range-map interval are fetched one
+  // partition ahead (next_s, next_u): the ticket by lane 0 of warp 0 before its look-back,
+  // the rest by asynchronous copies to shared memory that complete while the workers
+  // rank.  Tickets stay in increasing order within a block, so the block holding the
+  // smallest unfinished ticket is always working on it and every look-back ends.
+  auto fetch_next = [&](uint64_t nx) {  // one thread; completes at cp.async.wait_all
+    next_s[0] = nx;
+    if (nx < NF) {
+      cp_async8(&next_s[1], &b.foff[nx]);
+      cp_async8(&next_s[2], &b.foff[nx + 1]);
+      cp_async4(&next_u[0], &b.flo[nx]);
+      cp_async4(&next_u[1], &b.flo[nx + 1]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    fetch_next(atomicAdd(ticket, 1ull));
+    cp_async_wait_all();
+  }
   while (true) {
+    __syncthreads();
+    const uint64_t g = next_s[0];
+    if (g >= NF) break;
+    const uint64_t f0 = next_s[1];
+    uint64_t n = next_s[2] - f0;
     if (threadIdx.x == 0) {
-      g_s = atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->ticket), 1ull);
       ovf_s = 0;
       special_s = 0;
       nnew_s = 0;
     }
-    __syncthreads();
-    const uint64_t g = g_s;
-    if (g >= NF) break;
-    const uint64_t f0 = b.foff[g];
-    uint64_t n = b.foff[g + 1] - f0;
     if (f0 > s.cap || n > s.cap - f0) {  // inconsistent scan: record it, count nothing
       if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
       n = 0;
@@ -1466,40 +1509,55 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     if (!ovf_s && dn <= dcap) {
       const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
       if (threadIdx.x == 0) st_status(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
-      // order through this partition's spent input region (keys) and kbuf (counts)
+      const long long tm = clock64();
+      if (threadIdx.x == 0) {
+        // every key of the partition lies in the key range of its range-map interval.
+        // next_u still holds this partition's interval (the next one is fetched later, by
+        // warp 0 during the ranking); flo[NF] = 0, so the last interval ends at 2^32 - 1
+        const uint32_t ulo = next_u[0], uhi = next_u[1] - 1u;
+        uint32_t xlo, xhi;
+        x_range(ulo, uhi, s.canonical, xlo, xhi);
+        key_range(xlo, xhi, s.k, range_s[0], range_s[1]);
+      }
       K lo;
       int sh;
       uint32_t NB;
-      uint32_t rank[kRankPer];
-      bucket_table<KW>(tb, 1u << bT, dn, b.sbuf + f0 * KW, stage_cnt_all + f0, hist, red_lo, red_hi, wtmp, prof, lo, sh,
-                       NB);
+      bucket_slots<KW>(tb, 1u << bT, dn, range_s, hist, idx, wtmp, big_s, &big_n, lo, sh, NB, &b.meta->status,
+                       prof);
+      if (prof && threadIdx.x == 0) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
+      uint32_t rank[kRankRegs];
       if (wid == 0) {
         const long long lb0 = clock64();
+        uint64_t nx = 0;
+        if (lane == 0) nx = atomicAdd(ticket, 1ull);  // used after the look-back
         const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
         if (lane == 0) {
           if (g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
           excl_s = ex;
+          fetch_next(nx);
           if (s.profile)
             atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[4]), (unsigned long long)(clock64() - lb0));
         }
       } else {
-        load_and_rank<KW>(b.sbuf + f0 * KW, stage_cnt_all + f0, dn, dk, dc, hist, NB, lo, sh, rank, prof);
+        rank_slots<KW>(tb, idx, idx, dn, hist, NB, lo, sh, big_s, big_n, rank, prof);
       }
       __syncthreads();
       phase(3);
       const uint64_t ex = excl_s;
-      if (wid > 0) emit_ranked<KW>(dk, dc, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
-      if (special_s && threadIdx.x == 0) {
-        if (ex + dn < s.cap) {
-          store_key(b.out_keys, ex + dn, EMPTY);
-          b.out_counts[ex + dn] = special_s;
-        } else {
-          atomicOr(&b.meta->status, ST_INTERNAL);
+      if (wid > 0) emit_slots<KW>(tb, idx, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+      if (threadIdx.x == 0) {
+        if (special_s) {
+          if (ex + dn < s.cap) {
+            store_key(b.out_keys, ex + dn, EMPTY);
+            b.out_counts[ex + dn] = special_s;
+          } else {
+            atomicOr(&b.meta->status, ST_INTERNAL);
+          }
         }
+        cp_async_wait_all();
       }
-      __syncthreads();
       phase(5);
-      continue;
+      continue;  // the loop head synchronises
     }
     // ---------------- overflow path: too many distinct keys for the table.  Split the
     // partition's key range into sub-ranges, each counted in its own table and ordered;
@@ -1520,28 +1578,16 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         mx = key > mx ? key : mx;
       }
     }
-#pragma unroll
-    for (int dd = 16; dd > 0; dd >>= 1) {
-      const K a = shfl_key(mn, (lane + dd) & 31), c = shfl_key(mx, (lane + dd) & 31);
-      mn = a < mn ? a : mn;
-      mx = c > mx ? c : mx;
-    }
-    if (lane == 0) {
-      red_lo[wid] = mn;
-      red_hi[wid] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      K a = EMPTY, c = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        a = red_lo[w] < a ? red_lo[w] : a;
-        c = red_hi[w] > c ? red_hi[w] : c;
-      }
-      stk_n = 0;
-      if (a <= c) {
-        stk_lo[0] = a;
-        stk_hi[0] = c;
-        stk_n = 1;
+    {
+      K a, c;
+      block_range<K>(mn, mx, red_lo, red_hi, a, c);
+      if (threadIdx.x == 0) {
+        stk_n = 0;
+        if (a <= c) {
+          stk_lo[0] = a;
+          stk_hi[0] = c;
+          stk_n = 1;
+        }
       }
     }
     __syncthreads();
@@ -1580,25 +1626,21 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         __syncthreads();
         continue;
       }
-      // stage in the output region this sub-range will occupy, order, write back in place
       const uint64_t base = excl_s + written;
-      if (base + dn2 > s.cap) {
-        if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
-        __syncthreads();
-        continue;
-      }
       {
+        if (threadIdx.x == 0) {
+          range_s[0] = lo;
+          range_s[1] = hi;
+        }
         K lo2;
         int sh2;
         uint32_t NB2;
-        uint32_t rank2[kRankPer];
-        bucket_table<KW>(tb, cap_slots, dn2, b.out_keys + base * KW, b.out_counts + base, hist, red_lo, red_hi, wtmp,
-                         nullptr, lo2, sh2, NB2);
-        if (wid > 0)
-          load_and_rank<KW>(b.out_keys + base * KW, b.out_counts + base, dn2, dk, dc, hist, NB2, lo2, sh2, rank2,
-                            nullptr);
+        bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
+                         &b.meta->status);
+        uint32_t rank2[kRankRegs];
+        if (wid > 0) rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
         __syncthreads();
-        if (wid > 0) emit_ranked<KW>(dk, dc, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+        if (wid > 0) emit_slots<KW>(tb, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       }
       written += dn2;
       __syncthreads();
@@ -1628,8 +1670,9 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         ++written;
       }
       st_status(&b.look[g], kLookIncl | (excl_s + written));
+      fetch_next(atomicAdd(ticket, 1ull));
+      cp_async_wait_all();
     }
-    __syncthreads();
     phase(6);
   }
 }
@@ -1739,7 +1782,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
     ++launches;
     KC_STEP("k_scatter");
   }
-  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_log2, P1, s.fine_target, nf_max,
+  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_log2, b.flo, P1, s.b1, s.fine_target, nf_max,
                                                b.meta);
   ++launches;
   KC_STEP("k_fine_plan");

@@ -154,6 +154,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   const size_t o_cst = take((size_t)(P1 + 1) * 8), o_fb = take((size_t)(P1 + 1) * 4), o_fl = take((size_t)P1);
   const size_t o_hll = take((size_t)kc::kHllRegs * 4);
   const size_t o_fh = take((size_t)nf_max * 4), o_fo = take((size_t)(nf_max + 1) * 8);
+  const size_t o_flo = take((size_t)(nf_max + 1) * 4);
   const size_t o_fc = take((size_t)nf_max * 8), o_look = take((size_t)nf_max * 8);
   const size_t o_kbuf = take(cap * s.kw * 8), o_sbuf = take(cap * s.kw * 8), o_meta = take(sizeof(kc::Meta));
   if (o > (size_t)KC_NOALLOC_SCRATCH_BYTES)
@@ -173,6 +174,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);
+  b.flo = (uint32_t*)(ws + o_flo);
   b.fcur = (unsigned long long*)(ws + o_fc);
   b.look = (unsigned long long*)(ws + o_look);
   b.kbuf = (uint64_t*)(ws + o_kbuf);

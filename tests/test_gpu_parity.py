@@ -128,6 +128,25 @@ def test_heavy_hitter_single_key(counter):
         assert_parity(counter, r, o, k, True, f"mixed heavy k={k}")
 
 
+def test_keys_clumped_under_a_long_prefix(counter):
+    # reads that open with a long A run and go on at random: thousands of distinct canonical
+    # keys share their leading zero bits, so within the first partition they fall in a
+    # handful of order buckets far above average size (sorted by a warp, not ranked by
+    # counting), and the partition overflows its table (split into key sub-ranges)
+    rng = np.random.default_rng(11)
+    bases = np.frombuffer(b"ACGT", dtype=np.uint8)
+    strings = []
+    for i in range(4000):
+        tail = bases[rng.integers(0, 4, size=int(rng.integers(20, 60)))].tobytes()
+        strings.append(b"A" * int(rng.integers(20, 40)) + tail)
+        if i % 4 == 0:  # the reverse-complement form of the same clump
+            strings.append(tail[::-1].translate(bytes.maketrans(b"ACGT", b"TGCA")) + b"T" * 30)
+    r, o = as_reads(strings)
+    for k in (21, 31, 33, 63):
+        assert_parity(counter, r, o, k, True, f"clumped k={k}")
+    assert_parity(counter, r, o, 31, False, "clumped fwd k=31")
+
+
 def test_all_ones_key(counter):
     # non-canonical k=32 / k=64: the all-T k-mer has every key bit set
     for k in (32, 64):
