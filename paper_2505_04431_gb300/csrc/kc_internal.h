@@ -26,7 +26,7 @@ constexpr int kMaxFineLog2 = 10;               // at most 1024 fine partitions p
 constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
 constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
 constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
-constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
+constexpr int kFineLocalCap = 1024;            // fine partitions one chunk may span (shared histogram)
 constexpr int kHllLog2 = 10;                   // distinct-key sketch: 1024 registers
 constexpr int kHllRegs = 1 << kHllLog2;
 constexpr int kHllSampleLog2 = 3;              // ... over a 1/8 hash sample of the keys

@@ -78,6 +78,10 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)), "l"(src)
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)), "l"(src)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
@@ -774,25 +778,33 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
 }
 
 // ------------------------------------------------------------------ phase 2: fine split
-struct FineCtx {
+// Fine partition of a key: the coarse field c of u selects {first fine partition of c,
+// shift}; the fine field is the next fine_log2[c] bits of u.  Shifts by 32 or more give 0
+// (clamping funnel shifts), which covers b1 = 0 and fine_log2 = 0.
+struct FineMap {
   int k, canonical, b1;
+  uint32_t lowmask;  // the bits of u below the coarse field
 };
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t s) { return __funnelshift_rc(x, 0u, s); }
 
 template <class K>
-__device__ __forceinline__ uint32_t fine_index(K key, const FineCtx& x, const uint32_t* fine_base_s, const uint8_t* flog_s) {
+__device__ __forceinline__ uint32_t fine_of(K key, const FineMap& x, const uint2* fmap) {
   const uint32_t u = umap(top32_of(key, x.k), x.canonical);
-  const uint32_t c = field32(u, 0, x.b1);
-  return fine_base_s[c] + field32(u, x.b1, flog_s[c]);
+  const uint2 e = fmap[shr_clamp(u, 32 - x.b1)];
+  return e.x + shr_clamp(u & x.lowmask, e.y);
 }
 
-template <int KW>
-__device__ __forceinline__ void load_fine_tables(const Buffers& b, int P1, uint32_t* fine_base_s, uint8_t* flog_s) {
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x) fine_base_s[c] = b.fine_base[c];
-  for (int c = threadIdx.x; c < P1; c += blockDim.x) flog_s[c] = b.fine_log2[c];
+// fmap[c] = {fine_base[c], 32 - b1 - fine_log2[c]} for c < P1, fmap[P1].x = fine partition count.
+__device__ __forceinline__ void load_fine_map(const Buffers& b, int P1, int b1, uint2* fmap) {
+  for (int c = threadIdx.x; c <= P1; c += blockDim.x)
+    fmap[c] = make_uint2(b.fine_base[c], c < P1 ? (uint32_t)(32 - b1 - b.fine_log2[c]) : 0u);
+}
+__host__ __device__ inline FineMap make_fine_map(const Shape& s) {
+  return FineMap{s.k, s.canonical, s.b1, (uint32_t)((1ull << (32 - s.b1)) - 1)};
 }
 
 constexpr int kFineThreads = 512;
-constexpr int kFinePer = 16;  // keys per thread per chunk (loaded as 16-byte pairs / quads, all before use)
+constexpr int kFinePer = 8;  // keys per thread per chunk (loaded as 16-byte pairs / single u128, all before use)
 constexpr int kFineChunk = kFineThreads * kFinePer;
 
 // Load this thread's keys of the chunk [c0, c1): pairs of words (read-only path, all
@@ -827,32 +839,46 @@ __device__ __forceinline__ void load_chunk(const uint64_t* __restrict__ src, uin
   }
 }
 
+// Chunks of the coarse-grouped keys are handed out round-robin.  A chunk's first and last
+// keys bound the fine partitions it touches; they are fetched for the block's next chunk
+// (cp.async into bnd_s[1 - cur]) while the current one is processed.
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads) k_fine_hist(Shape s, Buffers b) {
+__device__ __forceinline__ void fetch_bounds(const uint64_t* kbuf, uint64_t c0, uint64_t K_total,
+                                             typename KeyT<KW>::T* bnd) {
+  const uint64_t c1 = min(K_total, c0 + kFineChunk);
+  if constexpr (KW == 1) {
+    cp_async8(&bnd[0], kbuf + c0);
+    cp_async8(&bnd[1], kbuf + c1 - 1);
+  } else {
+    cp_async16(&bnd[0], kbuf + 2 * c0);
+    cp_async16(&bnd[1], kbuf + 2 * (c1 - 1));
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
-  uint32_t* fine_base_s = reinterpret_cast<uint32_t*>(sm);  // [P1+1]
-  uint32_t* lh = fine_base_s + P1 + 1;                       // [kFineLocalCap]
-  uint8_t* flog_s = reinterpret_cast<uint8_t*>(lh + kFineLocalCap);
-  __shared__ uint32_t g_lo_s, g_hi_s;
-  load_fine_tables<KW>(b, P1, fine_base_s, flog_s);
+  uint2* fmap = reinterpret_cast<uint2*>(sm);                    // [P1 + 1]
+  uint32_t* lh = reinterpret_cast<uint32_t*>(fmap + P1 + 1);     // [kFineLocalCap]
+  __shared__ __align__(16) K bnd_s[2][2];
+  load_fine_map(b, P1, s.b1, fmap);
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
-  const FineCtx x{s.k, s.canonical, s.b1};
+  const FineMap x = make_fine_map(s);
   const uint64_t K_total = b.meta->n_windows;
+  const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
+  if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+    cp_async_wait_all();
+  }
   __syncthreads();
-  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += (uint64_t)gridDim.x * kFineChunk) {
+  int cur = 0;
+  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
     const uint64_t c1 = min(K_total, c0 + kFineChunk);
-    if (threadIdx.x == 0) {
-      K kf, kl;
-      load_key(b.kbuf, c0, kf);
-      load_key(b.kbuf, c1 - 1, kl);
-      const uint32_t cf = coarse_of(kf, s.k, s.canonical, s.b1), cl = coarse_of(kl, s.k, s.canonical, s.b1);
-      g_lo_s = fine_base_s[cf];
-      g_hi_s = fine_base_s[cl + 1];
-    }
-    __syncthreads();
-    const uint32_t g_lo = g_lo_s, span = g_hi_s - g_lo_s;
+    const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
+    const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
+    if (threadIdx.x == 0 && c0 + stride < K_total) fetch_bounds<KW>(b.kbuf, c0 + stride, K_total, bnd_s[cur ^ 1]);
     const bool local = span <= (uint32_t)kFineLocalCap;
     K keys[kFinePer];
     uint32_t have;
@@ -860,7 +886,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_hist(Shape s, Buffers b) 
 #pragma unroll
     for (int m = 0; m < kFinePer; ++m) {
       if ((have >> m) & 1u) {
-        const uint32_t g = fine_index(keys[m], x, fine_base_s, flog_s);
+        const uint32_t g = fine_of(keys[m], x, fmap);
         if (local && g - g_lo < span) atomicAdd(&lh[g - g_lo], 1u);
         else if (g < s.nf_max) atomicAdd(&b.fhist[g], 1u);
         else atomicOr(&b.meta->status, ST_INTERNAL);
@@ -877,6 +903,7 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_hist(Shape s, Buffers b) 
         }
       }
     }
+    if (threadIdx.x == 0) cp_async_wait_all();
     __syncthreads();
   }
 }
@@ -933,37 +960,74 @@ __global__ void k_fine_scan(Shape sh, Buffers b) {
   if (t == 0) b.foff[NF] = carry_s;
 }
 
+// Exclusive scan of in[0, n) into out[0, n) (all threads of the block, n <= 4 * blockDim);
+// returns the total.
+__device__ uint32_t block_scan_to(const uint32_t* in, uint32_t* out, int n, uint32_t* warp_tmp) {
+  const int nt = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = (nt + 31) >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  uint32_t x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_tmp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (wid ? warp_tmp[wid - 1] : 0);
+  const uint32_t total = warp_tmp[nw - 1];
+  for (int i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  __syncthreads();
+  return total;
+}
+
+// Split each chunk by fine partition: rank the keys in a shared histogram, bump each fine
+// partition's global cursor once per chunk, stage the keys grouped by fine partition and
+// write every group as one contiguous run.
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers b) {
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
-  K* stage = reinterpret_cast<K*>(sm);                                        // [kFineChunk]
-  uint64_t* gbase = reinterpret_cast<uint64_t*>(stage + kFineChunk);          // [kFineLocalCap]
-  uint32_t* lh = reinterpret_cast<uint32_t*>(gbase + kFineLocalCap);          // [padded kFineLocalCap]
-  uint32_t* soff = lh + padded_len(kFineLocalCap);                            // [padded kFineLocalCap]
-  uint16_t* stage_g = reinterpret_cast<uint16_t*>(soff + padded_len(kFineLocalCap));  // [kFineChunk]
-  uint32_t* fine_base_s = reinterpret_cast<uint32_t*>(stage_g + kFineChunk);  // [P1+1]
-  uint8_t* flog_s = reinterpret_cast<uint8_t*>(fine_base_s + P1 + 1);         // [P1]
-  __shared__ uint32_t g_lo_s, g_hi_s;
+  K* stage = reinterpret_cast<K*>(sm);                                          // [kFineChunk]
+  uint16_t* stage_g = reinterpret_cast<uint16_t*>(stage + kFineChunk);          // [kFineChunk]
+  uint64_t* delta = reinterpret_cast<uint64_t*>(stage_g + kFineChunk);          // [kFineLocalCap]
+  uint32_t* lh = reinterpret_cast<uint32_t*>(delta + kFineLocalCap);            // [kFineLocalCap]
+  uint32_t* soff = lh + kFineLocalCap;                                          // [kFineLocalCap]
+  uint2* fmap = reinterpret_cast<uint2*>(soff + kFineLocalCap);                 // [P1 + 1]
+  __shared__ __align__(16) K bnd_s[2][2];
   __shared__ uint32_t wt[32];
-  load_fine_tables<KW>(b, P1, fine_base_s, flog_s);
-  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[PAD(i)] = 0;
-  const FineCtx x{s.k, s.canonical, s.b1};
+  load_fine_map(b, P1, s.b1, fmap);
+  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
+  const FineMap x = make_fine_map(s);
   const uint64_t K_total = b.meta->n_windows;
+  const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
+  if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+    cp_async_wait_all();
+  }
   __syncthreads();
-  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += (uint64_t)gridDim.x * kFineChunk) {
+  int cur = 0;
+  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
     const uint64_t c1 = min(K_total, c0 + kFineChunk);
-    if (threadIdx.x == 0) {
-      K kf, kl;
-      load_key(b.kbuf, c0, kf);
-      load_key(b.kbuf, c1 - 1, kl);
-      const uint32_t cf = coarse_of(kf, s.k, s.canonical, s.b1), cl = coarse_of(kl, s.k, s.canonical, s.b1);
-      g_lo_s = fine_base_s[cf];
-      g_hi_s = fine_base_s[cl + 1];
-    }
-    __syncthreads();
-    const uint32_t g_lo = g_lo_s, span = g_hi_s - g_lo_s;
+    const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
+    const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
+    if (threadIdx.x == 0 && c0 + stride < K_total) fetch_bounds<KW>(b.kbuf, c0 + stride, K_total, bnd_s[cur ^ 1]);
     if (span == 0 || span > (uint32_t)kFineLocalCap) {
       // a chunk over very many tiny fine partitions: one global cursor bump per key
       for (int m = 0; m < kFinePer; ++m) {
@@ -971,64 +1035,56 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(Shape s, Buffers 
         if (i < c1) {
           K key;
           load_key(b.kbuf, i, key);
-          const uint32_t g = fine_index(key, x, fine_base_s, flog_s);
+          const uint32_t g = fine_of(key, x, fmap);
           const uint64_t pos = g < s.nf_max ? atomicAdd(&b.fcur[g], 1ull) : ~0ull;
           if (pos < s.cap) store_key(b.sbuf, pos, key);
           else atomicOr(&b.meta->status, ST_INTERNAL);
         }
       }
-      __syncthreads();
-      continue;
-    }
-    K keys[kFinePer];
-    uint32_t gr[kFinePer];
-    uint32_t have;
-    load_chunk<KW>(b.kbuf, c0, c1, keys, have);
+    } else {
+      K keys[kFinePer];
+      uint32_t gr[kFinePer];
+      uint32_t have;
+      load_chunk<KW>(b.kbuf, c0, c1, keys, have);
 #pragma unroll
-    for (int m = 0; m < kFinePer; ++m) {
-      gr[m] = 0xffffffffu;
-      if ((have >> m) & 1u) {
-        const uint32_t lg = fine_index(keys[m], x, fine_base_s, flog_s) - g_lo;
-        if (lg < span) {
-          const uint32_t r = atomicAdd(&lh[PAD(lg)], 1u);
-          gr[m] = (lg << 16) | r;
-        } else {
-          atomicOr(&b.meta->status, ST_INTERNAL);
+      for (int m = 0; m < kFinePer; ++m) {
+        gr[m] = 0xffffffffu;
+        if ((have >> m) & 1u) {
+          const uint32_t lg = fine_of(keys[m], x, fmap) - g_lo;
+          if (lg < span) gr[m] = (lg << 16) | atomicAdd(&lh[lg], 1u);  // span <= 2^10, rank < 2^16
+          else atomicOr(&b.meta->status, ST_INTERNAL);
         }
       }
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) soff[PAD(i)] = lh[PAD(i)];
-    __syncthreads();
-    block_exclusive_scan_pad<uint32_t>(soff, (int)span, wt);
-    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
-      const uint32_t v = lh[PAD(i)];
-      if (v) gbase[i] = g_lo + i < s.nf_max ? atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v) : ~0ull;
-    }
+      __syncthreads();
+      const uint32_t n_staged = block_scan_to(lh, soff, (int)span, wt);
+      // one cursor bump per fine partition; delta[lg] + staged position = global position
+      for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
+        const uint32_t v = lh[i];
+        if (v) {
+          uint64_t gb = s.cap;  // positions at or past cap are rejected below
+          if (g_lo + i < s.nf_max) gb = atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v);
+          else atomicOr(&b.meta->status, ST_INTERNAL);
+          delta[i] = gb - soff[i];
+          lh[i] = 0;
+        }
+      }
 #pragma unroll
-    for (int m = 0; m < kFinePer; ++m) {
-      if (gr[m] != 0xffffffffu) {
-        const uint32_t lg = gr[m] >> 16;
-        const uint32_t pos = soff[PAD(lg)] + (gr[m] & 0xffffu);
-        stage[pos] = keys[m];
-        stage_g[pos] = (uint16_t)lg;
+      for (int m = 0; m < kFinePer; ++m) {
+        if (gr[m] != 0xffffffffu) {
+          const uint32_t lg = gr[m] >> 16;
+          const uint32_t pos = soff[lg] + (gr[m] & 0xffffu);
+          stage[pos] = keys[m];
+          stage_g[pos] = (uint16_t)lg;
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < n_staged; i += kFineThreads) {
+        const uint64_t pos = delta[stage_g[i]] + i;
+        if (pos < s.cap) store_key(b.sbuf, pos, stage[i]);
+        else atomicOr(&b.meta->status, ST_INTERNAL);
       }
     }
-    __syncthreads();
-    // only the keys that were staged (a key outside the chunk's fine range was rejected above)
-    const uint32_t n_staged = soff[PAD(span - 1)] + lh[PAD(span - 1)];
-    for (uint32_t i = threadIdx.x; i < n_staged; i += kFineThreads) {
-      const uint32_t lg = stage_g[i];
-      if (lg >= span) {
-        atomicOr(&b.meta->status, ST_INTERNAL);
-        continue;
-      }
-      const uint64_t pos = gbase[lg] + (i - soff[PAD(lg)]);
-      if (pos < s.cap) store_key(b.sbuf, pos, stage[i]);
-      else atomicOr(&b.meta->status, ST_INTERNAL);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) lh[PAD(i)] = 0;
+    if (threadIdx.x == 0) cp_async_wait_all();
     __syncthreads();
   }
 }
@@ -1694,10 +1750,9 @@ static size_t scatter_smem(int kw, int nt, int P1) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
   return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4;
 }
-static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 4 + kFineLocalCap * 4 + P1 + 16; }
+static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 8 + kFineLocalCap * 4 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
-  return (size_t)kFineChunk * (kw * 8) + kFineLocalCap * 8 + 2 * padded_len(kFineLocalCap) * 4 + kFineChunk * 2 +
-         (size_t)(P1 + 1) * 4 + P1 + 16;
+  return (size_t)kFineChunk * (kw * 8 + 2) + kFineLocalCap * (8 + 4 + 4) + (size_t)(P1 + 1) * 8 + 16;
 }
 
 int configure_kernels(int device) {
