@@ -298,13 +298,13 @@ __device__ __forceinline__ uint32_t umap(uint32_t x, int canonical) {
   const uint32_t y = ~x;
   return ~__umulhi(y, y);
 }
-__device__ __forceinline__ uint32_t field32(uint32_t u, int skip, int bits) {
-  const uint32_t v = skip >= 32 ? 0u : (u << skip);
-  return bits ? v >> (32 - bits) : 0u;
-}
+// x >> s, and 0 for s >= 32 (one clamping funnel shift)
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t s) { return __funnelshift_rc(x, 0u, s); }
+// the coarse field of u: its top b1 bits (none for b1 = 0)
+__device__ __forceinline__ uint32_t coarse_field(uint32_t u, int b1) { return shr_clamp(u, 32 - b1); }
 template <class K>
 __device__ __forceinline__ uint32_t coarse_of(K key, int k, int canonical, int b1) {
-  return field32(umap(top32_of(key, k), canonical), 0, b1);
+  return coarse_field(umap(top32_of(key, k), canonical), b1);
 }
 
 // floor(sqrt(v)) from 32-bit conversions and single-precision arithmetic (64-bit
@@ -455,6 +455,22 @@ __device__ __forceinline__ void win_top(const Win& W, int i, int canonical, uint
     c1 = rlt ? r1 : f1;
   }
 }
+// Top 32 bits of (a:b) << sh, 0 <= sh < 64 (a compile-time constant once unrolled).
+__device__ __forceinline__ uint32_t top32_shl(uint64_t a, uint64_t b, int sh) {
+  return sh < 32 ? __funnelshift_l((uint32_t)a, (uint32_t)(a >> 32), sh)
+                 : __funnelshift_l((uint32_t)(b >> 32), (uint32_t)a, sh - 32);
+}
+// Window i: the top 32 bits of its canonical value only (the range-map input), from 32-bit
+// shifts.  The smaller of the forward and reverse-complement top words is the canonical
+// value's top word: where the top words differ they decide which value is smaller, and
+// where they tie both values share them.
+template <int KW, int WPT>
+__device__ __forceinline__ uint32_t win_top32(const Win& W, int i, int canonical) {
+  const uint32_t m = (uint32_t)(W.m0 >> 32);
+  const uint32_t f = top32_shl(W.s0, W.s1, 2 * i) & m;
+  const uint32_t r = top32_shl(W.r0, W.r1, 2 * (WPT - 1 - i)) & m;
+  return canonical ? min(f, r) : f;
+}
 __device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t, int k, uint64_t& key) {
   key = k >= 32 ? c0 : c0 >> (64 - 2 * k);
 }
@@ -516,11 +532,8 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
       win_setup<KW, 32>(code_s[t], code_s[t + 1], code, vm, 0, s.k, W);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        if ((W.valid >> i) & 1u) {
-          uint64_t c0, c1;
-          win_top<KW, 32>(W, i, s.canonical, c0, c1);
-          atomicAdd(&hist_s[field32(umap((uint32_t)(c0 >> 32), s.canonical), 0, s.b1)], 1u);
-        }
+        if ((W.valid >> i) & 1u)
+          atomicAdd(&hist_s[coarse_field(umap(win_top32<KW, 32>(W, i, s.canonical), s.canonical), s.b1)], 1u);
       }
     }
   }
@@ -732,7 +745,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
           uint64_t c0, c1;
           win_top<KW, WPT>(W, i, s.canonical, c0, c1);
           top_to_key(c0, c1, s.k, keys[i]);
-          const uint32_t c = field32(umap((uint32_t)(c0 >> 32), s.canonical), 0, s.b1);
+          const uint32_t c = coarse_field(umap((uint32_t)(c0 >> 32), s.canonical), s.b1);
           const uint32_t r = atomicAdd(&hist[PAD(c)], 1u);
           rr[i >> 1] |= r << (16 * (i & 1));
           const uint64_t hh = key_hash(keys[i]);
@@ -758,17 +771,19 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
     }
     __syncthreads();
     const uint32_t n_sub = soff[PAD(P1 - 1)] + hist[PAD(P1 - 1)];
+    // during the write-out cursor[c] holds cursor[c] - soff[c]: staged position i of
+    // partition c goes to cursor[c] + i
+    for (int c = t; c < P1; c += NT) cursor[c] -= soff[PAD(c)];
+    __syncthreads();
     for (uint32_t i = t; i < n_sub; i += NT) {
       const K key = stage[i];
-      const uint32_t c = coarse_of(key, s.k, s.canonical, s.b1);  // runs are grouped by partition
-      const uint32_t so = soff[PAD(c)];
-      const uint64_t pos = cursor[c] + (i - so);
-      if (i >= so && i - so < hist[PAD(c)] && pos < s.cap) store_key(b.kbuf, pos, key);
+      const uint64_t pos = cursor[coarse_of(key, s.k, s.canonical, s.b1)] + i;  // runs are grouped by partition
+      if (pos < s.cap) store_key(b.kbuf, pos, key);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
     __syncthreads();
     for (int c = t; c < P1; c += NT) {
-      cursor[c] += hist[PAD(c)];
+      cursor[c] += soff[PAD(c)] + hist[PAD(c)];
       hist[PAD(c)] = 0;
     }
   }
@@ -785,7 +800,6 @@ struct FineMap {
   int k, canonical, b1;
   uint32_t lowmask;  // the bits of u below the coarse field
 };
-__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t s) { return __funnelshift_rc(x, 0u, s); }
 
 template <class K>
 __device__ __forceinline__ uint32_t fine_of(K key, const FineMap& x, const uint2* fmap) {
