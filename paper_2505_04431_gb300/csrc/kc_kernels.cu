@@ -1109,34 +1109,54 @@ constexpr uint64_t kLookAgg = 1ull << 62;
 constexpr uint64_t kLookIncl = 2ull << 62;
 
 // Decoupled look-back (executed by one warp): sum of distinct counts of fine partitions < g.
+// Each step reads the kLookPer * 32 status words before position j at once (lane l holds
+// distance q * 32 + l); the nearest inclusive prefix among them ends the walk, and only
+// unpublished words nearer than it are waited for (with a bounded spin).
+constexpr int kLookPer = 8;
 __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* status) {
   const int lane = threadIdx.x & 31;
+  constexpr uint32_t kNone = kLookPer * 32;
   uint64_t excl = 0;
   int64_t j = (int64_t)g - 1;
   while (j >= 0) {
-    const int64_t idx = j - lane;
-    uint64_t v = kLookIncl;  // before the first partition: inclusive prefix 0
-    if (idx >= 0) {
-      uint32_t spins = 0;
-      v = ld_status(&look[idx]);
-      while ((v >> 62) == 0) {
-        if (++spins > kLookbackSpinLimit) {
-          atomicOr(status, ST_TIMEOUT);
-          v = kLookIncl;
-          break;
-        }
-        __nanosleep(64);
-        v = ld_status(&look[idx]);
+    uint64_t v[kLookPer];
+#pragma unroll
+    for (int q = 0; q < kLookPer; ++q) {
+      const int64_t idx = j - (q * 32 + lane);
+      v[q] = idx >= 0 ? ld_status(&look[idx]) : kLookIncl;  // before the first partition: inclusive 0
+    }
+    uint32_t stop = kNone, spins = 0;
+    while (true) {
+      stop = kNone;  // nearest inclusive distance
+#pragma unroll
+      for (int q = kLookPer - 1; q >= 0; --q) {
+        const unsigned b = __ballot_sync(0xffffffffu, (v[q] >> 62) == 2);
+        if (b) stop = q * 32 + __ffs(b) - 1;
+      }
+      bool wait = false;
+#pragma unroll
+      for (int q = 0; q < kLookPer; ++q) wait |= (uint32_t)(q * 32 + lane) < stop && (v[q] >> 62) == 0;
+      if (!__any_sync(0xffffffffu, wait)) break;
+      if (++spins > kLookbackSpinLimit) {
+        if (lane == 0) atomicOr(status, ST_TIMEOUT);
+        return excl;
+      }
+      __nanosleep(64);
+#pragma unroll
+      for (int q = 0; q < kLookPer; ++q) {
+        const int64_t idx = j - (q * 32 + lane);
+        if ((uint32_t)(q * 32 + lane) < stop && (v[q] >> 62) == 0) v[q] = ld_status(&look[idx]);
       }
     }
-    const unsigned incl = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-    const int stop = incl ? __ffs(incl) - 1 : 31;
-    uint64_t val = lane <= stop ? (v & kLookValue) : 0;
+    uint64_t val = 0;
+#pragma unroll
+    for (int q = 0; q < kLookPer; ++q)
+      if ((uint32_t)(q * 32 + lane) <= stop) val += v[q] & kLookValue;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) val += __shfl_xor_sync(0xffffffffu, val, d);
     excl += val;
-    if (incl) break;
-    j -= 32;
+    if (stop != kNone) break;
+    j -= kNone;
   }
   return excl;
 }
@@ -1168,7 +1188,7 @@ int table_log2_max(int kw, size_t smem_optin) {
 
 constexpr int kProbeLimit = 128;
 constexpr int kWorkers = kCountThreads - 32;  // warps 1.. load and sort while warp 0 looks back
-constexpr int kSlotsPerThread = (1 << kTableLog2Cap) / kCountThreads;
+constexpr int kSlotsPerWorker = ((1 << kTableLog2Cap) + kWorkers - 1) / kWorkers;
 
 // counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes)
 __device__ __forceinline__ uint32_t hslot(uint64_t key, int bT) {
@@ -1357,8 +1377,46 @@ constexpr uint32_t kBigBucket = 256;  // buckets above this are sorted by a warp
 
 constexpr int kBigMax = 32;  // more than d / kBigBucket <= 6144 / 257
 
-// Order the table's d occupied slots for output (all threads).  The key range [lo, hi]
-// of the table is read from range_s[0..1] (written by one thread before the call).  NB
+// Exclusive scan of the padded array data (logical element i at data[PAD(i)]) by the
+// worker warps (warp 0 is busy with the look-back meanwhile); returns the total.
+__device__ uint32_t workers_exclusive_scan_pad(uint32_t* data, int n, uint32_t* warp_tmp) {
+  constexpr int nt = kWorkers, nw = kWorkers / 32;
+  const int t = threadIdx.x - 32, lane = t & 31, wid = t >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += data[PAD(i)];
+  uint32_t x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  bar_workers();
+  if (wid == 0) {
+    uint32_t w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_tmp[lane] = w;
+  }
+  bar_workers();
+  uint32_t run = x - s + (wid ? warp_tmp[wid - 1] : 0);
+  const uint32_t total = warp_tmp[nw - 1];
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t v = data[PAD(i)];
+    data[PAD(i)] = run;
+    run += v;
+  }
+  bar_workers();
+  return total;
+}
+
+// Order the table's d occupied slots for output (worker warps only).  The key range
+// [lo, hi] of the table is read from range_s[0..1] (written by worker 0 before the call).  NB
 // buckets (key - lo) >> sh, one to two per key; an ordered counting sort of the slot
 // numbers into idx[0, d), bucket by bucket (buckets ascending, slots unordered inside a
 // bucket); hist[PAD(b)] is left holding bucket b's first position, and big_s[0, *big_n)
@@ -1371,8 +1429,9 @@ __device__ void bucket_slots(Table<KW> tb, uint32_t nslots, uint32_t d, const ty
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
   long long tm = clock64();
+  const int t = threadIdx.x - 32;
   auto mark = [&](int i) {
-    if (prof && threadIdx.x == 0) {
+    if (prof && t == 0) {
       const long long now = clock64();
       atomicAdd(&prof[i], (unsigned long long)(now - tm));
       tm = now;
@@ -1380,18 +1439,18 @@ __device__ void bucket_slots(Table<KW> tb, uint32_t nslots, uint32_t d, const ty
   };
   NB = 1;
   while (NB < (uint32_t)hist_max(KW) && NB < d) NB <<= 1;
-  for (uint32_t i = threadIdx.x; i < NB; i += blockDim.x) hist[PAD(i)] = 0;
-  if (threadIdx.x == 0) *big_n = 0;
-  __syncthreads();
+  for (uint32_t i = t; i < NB; i += kWorkers) hist[PAD(i)] = 0;
+  if (t == 0) *big_n = 0;
+  bar_workers();
   mark(2);
   lo = range_s[0];
   const K hi = range_s[1];
   const int bB = 31 - __clz(NB);
   sh = d == 0 ? 0 : max(0, bitlen(K(hi - lo)) - bB);
-  uint32_t br[kSlotsPerThread];
+  uint32_t br[kSlotsPerWorker];
 #pragma unroll
-  for (int m = 0; m < kSlotsPerThread; ++m) {
-    const uint32_t s = threadIdx.x + m * blockDim.x;
+  for (int m = 0; m < kSlotsPerWorker; ++m) {
+    const uint32_t s = t + m * kWorkers;
     br[m] = 0xffffffffu;
     if (s < nslots) {
       const K key = tb.keys[s];
@@ -1411,14 +1470,14 @@ __device__ void bucket_slots(Table<KW> tb, uint32_t nslots, uint32_t d, const ty
       }
     }
   }
-  __syncthreads();
+  bar_workers();
   mark(5);
-  block_exclusive_scan_pad<uint32_t>(hist, (int)NB, wtmp);
+  workers_exclusive_scan_pad(hist, (int)NB, wtmp);
   mark(6);
 #pragma unroll
-  for (int m = 0; m < kSlotsPerThread; ++m)
-    if (br[m] != 0xffffffffu) idx[hist[PAD(br[m] >> 16)] + (br[m] & 0xffffu)] = (uint16_t)(threadIdx.x + m * blockDim.x);
-  __syncthreads();
+  for (int m = 0; m < kSlotsPerWorker; ++m)
+    if (br[m] != 0xffffffffu) idx[hist[PAD(br[m] >> 16)] + (br[m] & 0xffffu)] = (uint16_t)(t + m * kWorkers);
+  bar_workers();
   mark(7);
 }
 
@@ -1528,11 +1587,12 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       t_mark = now;
     }
   };
-  // The next partition's ticket, input range and range-map interval are fetched one
-  // partition ahead (next_s, next_u): the ticket by lane 0 of warp 0 before its look-back,
-  // the rest by asynchronous copies to shared memory that complete while the workers
-  // rank.  Tickets stay in increasing order within a block, so the block holding the
-  // smallest unfinished ticket is always working on it and every look-back ends.
+  // The next partition's ticket, input range and range-map interval (next_s, next_u) are
+  // fetched by thread 0 while the workers write the current partition out: the ticket is
+  // taken as late as that, so that partitions start in ticket order and a look-back seldom
+  // waits on a predecessor that started late; the rest arrives by asynchronous copies to
+  // shared memory.  Tickets stay in increasing order within a block, so the block holding
+  // the smallest unfinished ticket is always working on it and every look-back ends.
   auto fetch_next = [&](uint64_t nx) {  // one thread; completes at cp.async.wait_all
     next_s[0] = nx;
     if (nx < NF) {
@@ -1579,41 +1639,40 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     if (!ovf_s && dn <= dcap) {
       const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
       if (threadIdx.x == 0) st_status(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
-      const long long tm = clock64();
-      if (threadIdx.x == 0) {
-        // every key of the partition lies in the key range of its range-map interval.
-        // next_u still holds this partition's interval (the next one is fetched later, by
-        // warp 0 during the ranking); flo[NF] = 0, so the last interval ends at 2^32 - 1
-        const uint32_t ulo = next_u[0], uhi = next_u[1] - 1u;
-        uint32_t xlo, xhi;
-        x_range(ulo, uhi, s.canonical, xlo, xhi);
-        key_range(xlo, xhi, s.k, range_s[0], range_s[1]);
-      }
-      K lo;
-      int sh;
-      uint32_t NB;
-      bucket_slots<KW>(tb, 1u << bT, dn, range_s, hist, idx, wtmp, big_s, &big_n, lo, sh, NB, &b.meta->status,
-                       prof);
-      if (prof && threadIdx.x == 0) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
+      // warp 0 resolves the exclusive prefix (look-back) while the workers order the table
       uint32_t rank[kRankRegs];
       if (wid == 0) {
         const long long lb0 = clock64();
-        uint64_t nx = 0;
-        if (lane == 0) nx = atomicAdd(ticket, 1ull);  // used after the look-back
         const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
         if (lane == 0) {
           if (g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
           excl_s = ex;
-          fetch_next(nx);
           if (s.profile)
             atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[4]), (unsigned long long)(clock64() - lb0));
         }
       } else {
+        const long long tm = clock64();
+        if (threadIdx.x == 32) {
+          // every key of the partition lies in the key range of its range-map interval.
+          // next_u still holds this partition's interval (the next one is fetched during
+          // the write-out); flo[NF] = 0, so the last interval ends at 2^32 - 1
+          const uint32_t ulo = next_u[0], uhi = next_u[1] - 1u;
+          uint32_t xlo, xhi;
+          x_range(ulo, uhi, s.canonical, xlo, xhi);
+          key_range(xlo, xhi, s.k, range_s[0], range_s[1]);
+        }
+        K lo;
+        int sh;
+        uint32_t NB;
+        bucket_slots<KW>(tb, 1u << bT, dn, range_s, hist, idx, wtmp, big_s, &big_n, lo, sh, NB, &b.meta->status,
+                         prof);
+        if (prof && threadIdx.x == 32) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
         rank_slots<KW>(tb, idx, idx, dn, hist, NB, lo, sh, big_s, big_n, rank, prof);
       }
       __syncthreads();
       phase(3);
       const uint64_t ex = excl_s;
+      if (threadIdx.x == 0) fetch_next(atomicAdd(ticket, 1ull));
       if (wid > 0) emit_slots<KW>(tb, idx, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       if (threadIdx.x == 0) {
         if (special_s) {
@@ -1698,17 +1757,19 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       }
       const uint64_t base = excl_s + written;
       {
-        if (threadIdx.x == 0) {
-          range_s[0] = lo;
-          range_s[1] = hi;
-        }
-        K lo2;
-        int sh2;
-        uint32_t NB2;
-        bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
-                         &b.meta->status);
         uint32_t rank2[kRankRegs];
-        if (wid > 0) rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
+        if (wid > 0) {
+          if (threadIdx.x == 32) {
+            range_s[0] = lo;
+            range_s[1] = hi;
+          }
+          K lo2;
+          int sh2;
+          uint32_t NB2;
+          bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
+                           &b.meta->status);
+          rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
+        }
         __syncthreads();
         if (wid > 0) emit_slots<KW>(tb, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       }
