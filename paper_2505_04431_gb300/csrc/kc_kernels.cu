@@ -1250,11 +1250,12 @@ __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
 }
 
 // Count the keys in[0, n) (only those in [lo, hi] when `ranged`).  The all-ones key is
-// counted apart in *special (it marks empty slots).  Sets *ovf if a key found no slot.
+// counted apart in *special (it marks empty slots); it exists only when the k-mer fills
+// the key word (full_width).  Sets *ovf if a key found no slot.
 template <int KW>
 __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
-                          typename KeyT<KW>::T hi, int bT, uint32_t* n_new, uint32_t* ovf, uint32_t* special,
-                          uint32_t* status) {
+                          typename KeyT<KW>::T hi, int bT, bool full_width, uint32_t* n_new, uint32_t* ovf,
+                          uint32_t* special, uint32_t* status) {
   typedef typename KeyT<KW>::T K;
   constexpr int kIn = KW == 1 ? 8 : 2;  // loads in flight per thread (u128 keys: register-bound at 64)
   const K EMPTY = all_ones<K>();
@@ -1275,22 +1276,21 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
       const K key = kk[m];
       bool act = aa[m];
       if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
-      const unsigned am = __ballot_sync(0xffffffffu, act);
-      if (!am) continue;
-      const int first = __ffs(am) - 1;
-      const K k0 = shfl_key(key, first);
-      const bool same = __all_sync(0xffffffffu, !act || key == k0);
-      if (same) {  // a warp of equal keys (heavy hitter) adds once
-        if (lane == first) {
+      // a warp whose active keys all equal lane 0's key (a heavy hitter) adds them at once;
+      // lane 0's own key counts only if it is active, so any inactive lane 0 is harmless
+      const K k0 = shfl_key(key, 0);
+      if (__all_sync(0xffffffffu, !act || key == k0)) {
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        if (am && lane == __ffs(am) - 1) {
           const uint32_t inc = __popc(am);
-          if (k0 == EMPTY) {
+          if (full_width && k0 == EMPTY) {
             if (atomicAdd(special, inc) > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
           } else if (!count_insert<KW>(tb, k0, inc, bT, n_new, check, status)) {
             atomicOr(ovf, 1u);
           }
         }
       } else if (act) {
-        if (key == EMPTY) {
+        if (full_width && key == EMPTY) {
           if (atomicAdd(special, 1u) == 0xffffffffu) atomicOr(status, ST_COUNT_OVERFLOW);
         } else if (!count_insert<KW>(tb, key, 1u, bT, n_new, check, status)) {
           atomicOr(ovf, 1u);
@@ -1632,7 +1632,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     table_clear<KW>(tb, 1u << bT);
     __syncthreads();
     phase(0);
-    count_all<KW>(tb, in, n, false, K(0), K(0), bT, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+    count_all<KW>(tb, in, n, false, K(0), K(0), bT, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
     __syncthreads();
     phase(1);
     const uint32_t dn = nnew_s;
@@ -1735,7 +1735,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
       }
       table_clear<KW>(tb, cap_slots);
       __syncthreads();
-      count_all<KW>(tb, in, n, true, lo, hi, bTf, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+      count_all<KW>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
       __syncthreads();
       const uint32_t dn2 = nnew_s;
       const K width = hi - lo;
