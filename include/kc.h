@@ -59,7 +59,8 @@ typedef struct {
   uint64_t max_device_bytes;  /* 0: no limit; else kc_count fails with KC_ENOMEM above it */
   uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 4096); 0: chosen from input size */
   uint32_t block_size_hint;   /* reserved (0) */
-  float table_load;           /* target load of the per-partition count tables; 0: 0.5 */
+  float table_load;           /* distinct keys aimed at per fine partition, as a fraction of the
+                                 count table's slots (the fine split is sized by it); 0: 0.55 */
   uint32_t table_slots_max;   /* 0: largest table that fits shared memory; smaller values
                                  (>= 64) force the overflow path, for testing */
   uint32_t flags;             /* KC_PLAN_* bits */
@@ -68,6 +69,10 @@ typedef struct {
 /* kc_plan_opts.flags: record a CUDA event on the plan's stream after every kernel
  * launch of kc_count, so kc_last_kernel_times can report each kernel's device time. */
 #define KC_PLAN_PROFILE 1u
+/* Testing: every fine partition writes its run to its own input region and the final
+ * compaction pass moves it (the path taken when a partition's output offset is not yet
+ * known when it is ready to write). */
+#define KC_PLAN_DEFER_ALL 2u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */
@@ -120,6 +125,8 @@ typedef struct {
   uint32_t n_partitions;       /* coarse partitions (phase 1) */
   uint64_t n_fine;             /* fine partitions (one shared-memory table each) */
   uint64_t n_overflow_fine;    /* fine partitions that needed the overflow path */
+  uint64_t n_deferred_fine;    /* fine partitions whose run was moved to its place after the count
+                                  (their output offset was not known in time) */
   uint64_t workspace_bytes;    /* scratch currently held by the plan */
   uint64_t phase_cycles[8];    /* KC_PLAN_PROFILE only: SM cycles of the count kernel's phases
                                   (clear, insert, sort, count, look-back, emit, overflow path,

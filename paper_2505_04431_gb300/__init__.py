@@ -30,6 +30,7 @@ EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan
             "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
+KC_PLAN_DEFER_ALL = 2
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -51,7 +52,7 @@ class Result(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint32), ("n_partitions", ctypes.c_uint32),
-                ("n_fine", ctypes.c_uint64), ("n_overflow_fine", ctypes.c_uint64),
+                ("n_fine", ctypes.c_uint64), ("n_overflow_fine", ctypes.c_uint64), ("n_deferred_fine", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("phase_cycles", ctypes.c_uint64 * 8),
                 ("sub_cycles", ctypes.c_uint64 * 8)]
 
@@ -181,7 +182,7 @@ class KmerCounter:
 
     def __init__(self, device: int | None = None, stream=None, use_torch_allocator: bool = True,
                  n_partitions_hint: int = 0, table_load: float = 0.0, table_slots_max: int = 0,
-                 max_device_bytes: int = 0, profile: bool = False):
+                 max_device_bytes: int = 0, profile: bool = False, defer_all: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("KmerCounter needs a CUDA device (no CPU fallback)")
@@ -218,7 +219,7 @@ class KmerCounter:
         opts.n_partitions_hint = int(n_partitions_hint)
         opts.table_load = float(table_load)
         opts.table_slots_max = int(table_slots_max)
-        opts.flags = KC_PLAN_PROFILE if profile else 0
+        opts.flags = (KC_PLAN_PROFILE if profile else 0) | (KC_PLAN_DEFER_ALL if defer_all else 0)
         plan = ctypes.c_void_p()
         _check(lib, lib.kc_plan(ctypes.byref(opts), ctypes.byref(plan)))
         self._opts = opts

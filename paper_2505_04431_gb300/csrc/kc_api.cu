@@ -2,6 +2,8 @@
 // checks, the phase-1 / phase-2 launch sequence and error reporting.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
@@ -48,6 +50,7 @@ struct kc_plan_s {
   kc_stats stats{};
   // per-kernel timing (KC_PLAN_PROFILE)
   bool profile = false;
+  bool defer_all = false;
   static constexpr int kMaxMarks = 32;
   cudaEvent_t ev[kMaxMarks + 1] = {};
   const char* ev_name[kMaxMarks] = {};
@@ -118,6 +121,15 @@ void record_mark(void* ctx, const char* name) {
   ++p->n_marks;
 }
 
+// Diagnostics (environment variable KC_DEBUG_SYNC set): wait for every kernel as soon as it
+// is launched and report it on stderr, so that a kernel that does not finish is named.
+void debug_mark(void* ctx, const char* name) {
+  kc_plan_s* p = (kc_plan_s*)ctx;
+  fprintf(stderr, "[kc] %s launched\n", name);
+  const cudaError_t e = cudaStreamSynchronize(p->stream);
+  fprintf(stderr, "[kc] %s finished: %s\n", name, cudaGetErrorString(e));
+}
+
 }  // namespace
 
 extern "C" {
@@ -154,11 +166,12 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->ctx = opts->alloc_ctx;
   p->max_bytes = opts->max_device_bytes;
   p->p_hint = opts->n_partitions_hint;
-  p->load = opts->table_load > 0.f ? opts->table_load : 0.5f;
+  p->load = opts->table_load > 0.f ? opts->table_load : 0.55f;
   p->slots_max = opts->table_slots_max;
   p->n_sms = prop.multiProcessorCount;
   p->smem_optin = prop.sharedMemPerBlockOptin;
   p->profile = (opts->flags & KC_PLAN_PROFILE) != 0;
+  p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
   if (p->profile) {
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) {
       if ((e = cudaEventCreate(&p->ev[i])) != cudaSuccess) {
@@ -284,16 +297,18 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   }
   s.bT_max = bT_max;
   s.tail = bT_max >= 10 ? 1024 : (1 << bT_max);
-  double ft = (double)(1u << bT_max) * p->load * 0.75;
+  const double ft = (double)(1u << bT_max) * p->load;  // distinct keys per fine partition aimed at
   s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
   s.cap = L > 0 ? L : 1;
-  // sum over partitions of 2^ceil(log2(ceil(n_c / ft))) <= 2 K / ft + 3 P1
-  const uint64_t nf_bound = 2 * s.cap / s.fine_target + 3 * (uint64_t)P1 + 1;
-  const uint64_t nf_max64 = nf_bound < ((uint64_t)P1 << kc::kMaxFineLog2) ? nf_bound : ((uint64_t)P1 << kc::kMaxFineLog2);
+  // sum over partitions of ceil(n_c / target), target >= fine_target: at most K / ft + P1
+  const uint64_t nf_bound = s.cap / s.fine_target + (uint64_t)P1 + 1;
+  const uint64_t nf_lim = (uint64_t)P1 * kc::kMaxFine;
+  const uint64_t nf_max64 = nf_bound < nf_lim ? nf_bound : nf_lim;
   const uint32_t nf_max = (uint32_t)nf_max64;
   s.nf_max = nf_max;
   s.smem_budget = p->smem_optin;
   s.profile = p->profile ? 1 : 0;
+  s.defer_all = p->defer_all ? 1 : 0;
 
   // ---- scratch layout
   Layout lay;
@@ -306,7 +321,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   const size_t o_toff = lay.add(s.n_tiles * P1 * 8);
   const size_t o_cst = lay.add((size_t)(P1 + 1) * 8);
   const size_t o_fb = lay.add((size_t)(P1 + 1) * 4);
-  const size_t o_fl = lay.add((size_t)P1);
+  const size_t o_fl = lay.add((size_t)P1 * 4);
   const size_t o_hll = lay.add((size_t)kc::kHllRegs * 4);
   const size_t o_fh = lay.add((size_t)nf_max * 4);
   const size_t o_fo = lay.add((size_t)(nf_max + 1) * 8);
@@ -346,7 +361,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   b.toff = (uint64_t*)(ws + o_toff);
   b.cstart = (uint64_t*)(ws + o_cst);
   b.fine_base = (uint32_t*)(ws + o_fb);
-  b.fine_log2 = (uint8_t*)(ws + o_fl);
+  b.fine_m = (uint32_t*)(ws + o_fl);
   b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);
@@ -388,6 +403,9 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
     mark.fn = record_mark;
     mark.ctx = p;
     cudaEventRecord(p->ev[0], st);
+  } else if (getenv("KC_DEBUG_SYNC")) {
+    mark.fn = debug_mark;
+    mark.ctx = p;
   }
   int launches = kc::launch_phase1(s, b, p->n_sms, (void*)st, mark);
   if (launches >= 0) {
@@ -412,6 +430,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   p->stats.n_partitions = (uint32_t)P1;
   p->stats.n_fine = m.n_fine;
   p->stats.n_overflow_fine = m.n_overflow;
+  p->stats.n_deferred_fine = m.n_deferred;
   for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
   for (int i = 0; i < 8; ++i) p->stats.sub_cycles[i] = m.sub_cycles[i];
   if (m.status & kc::ST_BAD_OFFSETS) return bail(KC_EINVAL, "kc_count: offsets must start at 0 and be non-decreasing");

@@ -22,7 +22,7 @@ constexpr int kTileWords = 8192;               // one phase-1 tile = 262144 base
 constexpr uint64_t kTileBases = (uint64_t)kTileWords * kWordBases;
 constexpr int kPackThreads = 512;              // pass A: one code word per thread per sub-step
 constexpr int kMaxCoarseLog2 = 12;             // at most 4096 coarse partitions
-constexpr int kMaxFineLog2 = 10;               // at most 1024 fine partitions per coarse one
+constexpr int kMaxFine = 1024;                 // at most this many fine partitions per coarse one
 constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
 constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
 constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
@@ -48,6 +48,7 @@ struct Meta {
   uint64_t n_distinct;  // D
   uint64_t n_fine;      // number of fine partitions
   uint64_t n_overflow;  // fine partitions that took the overflow path
+  uint64_t n_deferred;  // fine partitions written out by k_compact (prefix unknown in time)
   uint32_t status;
   uint32_t pad;
   uint64_t ticket;      // phase-2 work counter
@@ -72,6 +73,7 @@ struct Shape {
   uint64_t nf_max;      // capacity of the fine-partition arrays
   uint64_t smem_budget; // opt-in shared memory per block
   int profile;          // nonzero: k_count_emit accumulates per-phase cycle counts
+  int defer_all;        // nonzero (testing): every fine partition takes the deferred write-out
 };
 
 struct Buffers {
@@ -84,9 +86,9 @@ struct Buffers {
   uint64_t* toff;         // [n_tiles][P1]
   uint64_t* cstart;       // [P1 + 1] coarse partition starts
   uint32_t* fine_base;    // [P1 + 1] first fine index of each coarse partition
-  uint8_t* fine_log2;     // [P1]
+  uint32_t* fine_m;       // [P1] fine partitions of each coarse partition
   uint32_t* hll;          // [kHllRegs] distinct-key sketch (max-merged by pass B)
-  uint32_t* fhist;        // [nf_max] keys per fine partition
+  uint32_t* fhist;        // [nf_max] keys per fine partition (fine split); then distinct keys | deferred bit 31
   uint64_t* foff;         // [nf_max + 1] fine partition starts
   uint32_t* flo;          // [nf_max + 1] first range-map value u of each fine partition (0 after the last)
   unsigned long long* fcur;  // [nf_max] fine scatter cursors

@@ -594,7 +594,7 @@ __global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, 
 // Fine split of every coarse partition, after pass B: the distinct-key estimate (a sampled
 // HyperLogLog filled by pass B) gives the duplication factor K / D, and a fine partition
 // aims at fine_target distinct keys, i.e. fine_target * K / D keys.  One block.
-__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint8_t* fine_log2,
+__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
                             uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
   extern __shared__ uint64_t fsc[];  // [P1]
   __shared__ uint64_t wt[32];
@@ -631,28 +631,28 @@ __global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_
     const double K = (double)cstart[P1];
     double dup = d_est > 1.0 ? K / d_est : 1.0;
     dup = dup < 1.0 ? 1.0 : (dup > 32.0 ? 32.0 : dup);
-    target_s = (double)fine_target * (0.8 * dup > 1.0 ? 0.8 * dup : 1.0);
+    target_s = (double)fine_target * (0.9 * dup > 1.0 ? 0.9 * dup : 1.0);
     meta->d_estimate = (uint64_t)d_est;
   }
   __syncthreads();
   const double target = target_s;
   for (int c = threadIdx.x; c < P1; c += blockDim.x) {
     const uint64_t n = cstart[c + 1] - cstart[c];
-    const uint64_t m = (uint64_t)ceil((double)n / target);
-    int bf = m <= 1 ? 0 : 64 - __clzll(m - 1);
-    bf = min(bf, kMaxFineLog2);
-    fine_log2[c] = (uint8_t)bf;
-    fsc[c] = 1ull << bf;
+    uint64_t m = (uint64_t)ceil((double)n / target);
+    m = m < 1 ? 1 : (m > (uint64_t)kMaxFine ? (uint64_t)kMaxFine : m);
+    fine_m[c] = (uint32_t)m;
+    fsc[c] = m;
   }
   __syncthreads();
   const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1, wt);
   for (int c = threadIdx.x; c < P1; c += blockDim.x) {
     fine_base[c] = (uint32_t)fsc[c];
-    // fine partition fine_base[c] + f holds the values u with coarse field c and fine field f
-    const int bf = fine_log2[c];
+    // fine partition fine_base[c] + f holds the values u of coarse field c whose low part
+    // v = u mod 2^(32 - b1) has floor(v m / 2^(32 - b1)) = f, i.e. v >= ceil(f 2^(32 - b1) / m)
+    const uint64_t m = fine_m[c], w = 1ull << (32 - b1);
     const uint32_t u0 = (uint32_t)((uint64_t)c << (32 - b1));
-    for (uint32_t f = 0; f < (1u << bf); ++f)
-      if (fsc[c] + f < nf_max) flo[fsc[c] + f] = u0 | (uint32_t)((uint64_t)f << (32 - b1 - bf));
+    for (uint64_t f = 0; f < m; ++f)
+      if (fsc[c] + f < nf_max) flo[fsc[c] + f] = u0 + (uint32_t)((f * w + m - 1) / m);
   }
   if (threadIdx.x == 0) {
     if (NF <= nf_max) flo[NF] = 0;  // so that the last partition ends at u = 2^32 - 1
@@ -794,28 +794,25 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
 
 // ------------------------------------------------------------------ phase 2: fine split
 // Fine partition of a key: the coarse field c of u selects {first fine partition of c,
-// shift}; the fine field is the next fine_log2[c] bits of u.  Shifts by 32 or more give 0
-// (clamping funnel shifts), which covers b1 = 0 and fine_log2 = 0.
+// m_c}; the fine index is floor(v m_c / 2^(32 - b1)) for the low part v of u (below the
+// coarse field), taken as the high word of (v << b1) * m_c.  The m_c fine partitions of c
+// split its range of u into near-equal parts.
 struct FineMap {
   int k, canonical, b1;
-  uint32_t lowmask;  // the bits of u below the coarse field
 };
 
 template <class K>
 __device__ __forceinline__ uint32_t fine_of(K key, const FineMap& x, const uint2* fmap) {
   const uint32_t u = umap(top32_of(key, x.k), x.canonical);
-  const uint2 e = fmap[shr_clamp(u, 32 - x.b1)];
-  return e.x + shr_clamp(u & x.lowmask, e.y);
+  const uint2 e = fmap[coarse_field(u, x.b1)];
+  return e.x + __umulhi(u << x.b1, e.y);
 }
 
-// fmap[c] = {fine_base[c], 32 - b1 - fine_log2[c]} for c < P1, fmap[P1].x = fine partition count.
-__device__ __forceinline__ void load_fine_map(const Buffers& b, int P1, int b1, uint2* fmap) {
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x)
-    fmap[c] = make_uint2(b.fine_base[c], c < P1 ? (uint32_t)(32 - b1 - b.fine_log2[c]) : 0u);
+// fmap[c] = {fine_base[c], fine_m[c]} for c < P1, fmap[P1].x = fine partition count.
+__device__ __forceinline__ void load_fine_map(const Buffers& b, int P1, uint2* fmap) {
+  for (int c = threadIdx.x; c <= P1; c += blockDim.x) fmap[c] = make_uint2(b.fine_base[c], c < P1 ? b.fine_m[c] : 0u);
 }
-__host__ __device__ inline FineMap make_fine_map(const Shape& s) {
-  return FineMap{s.k, s.canonical, s.b1, (uint32_t)((1ull << (32 - s.b1)) - 1)};
-}
+__host__ __device__ inline FineMap make_fine_map(const Shape& s) { return FineMap{s.k, s.canonical, s.b1}; }
 
 constexpr int kFineThreads = 512;
 constexpr int kFinePer = 8;  // keys per thread per chunk (loaded as 16-byte pairs / single u128, all before use)
@@ -877,7 +874,7 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers 
   uint2* fmap = reinterpret_cast<uint2*>(sm);                    // [P1 + 1]
   uint32_t* lh = reinterpret_cast<uint32_t*>(fmap + P1 + 1);     // [kFineLocalCap]
   __shared__ __align__(16) K bnd_s[2][2];
-  load_fine_map(b, P1, s.b1, fmap);
+  load_fine_map(b, P1, fmap);
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
   const uint64_t K_total = b.meta->n_windows;
@@ -1026,7 +1023,7 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffe
   uint2* fmap = reinterpret_cast<uint2*>(soff + kFineLocalCap);                 // [P1 + 1]
   __shared__ __align__(16) K bnd_s[2][2];
   __shared__ uint32_t wt[32];
-  load_fine_map(b, P1, s.b1, fmap);
+  load_fine_map(b, P1, fmap);
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
   const uint64_t K_total = b.meta->n_windows;
@@ -1111,9 +1108,12 @@ constexpr uint64_t kLookIncl = 2ull << 62;
 // Decoupled look-back (executed by one warp): sum of distinct counts of fine partitions < g.
 // Each step reads the kLookPer * 32 status words before position j at once (lane l holds
 // distance q * 32 + l); the nearest inclusive prefix among them ends the walk, and only
-// unpublished words nearer than it are waited for (with a bounded spin).
+// unpublished words nearer than it are waited for (with a bounded spin).  With `abort`,
+// the wait also ends as soon as *abort becomes nonzero, and kNoPrefix is returned.
 constexpr int kLookPer = 8;
-__device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* status) {
+constexpr uint64_t kNoPrefix = ~0ull;
+__device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* status,
+                             const volatile uint32_t* abort = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kNone = kLookPer * 32;
   uint64_t excl = 0;
@@ -1137,6 +1137,7 @@ __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* sta
 #pragma unroll
       for (int q = 0; q < kLookPer; ++q) wait |= (uint32_t)(q * 32 + lane) < stop && (v[q] >> 62) == 0;
       if (!__any_sync(0xffffffffu, wait)) break;
+      if (abort && *abort) return kNoPrefix;
       if (++spins > kLookbackSpinLimit) {
         if (lane == 0) atomicOr(status, ST_TIMEOUT);
         return excl;
@@ -1199,7 +1200,20 @@ __device__ __forceinline__ uint32_t hslot(u128 key, int bT) {
   return (uint32_t)(h >> (64 - bT));
 }
 
-__device__ __forceinline__ void bar_workers() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory"); }
+// Block barrier with the warp reconverged first: the count kernel reaches its barriers
+// straight after branches taken by one thread or lane (ticket fetch, look-back bookkeeping).
+__device__ __forceinline__ void block_sync() {
+  __syncwarp();
+  __syncthreads();
+}
+
+// Named barrier of the worker warps (1..31).  Its non-aligned form is used: a worker warp
+// may arrive diverged (right after a branch taken by one of its threads, e.g. thread 32
+// computing the key range), which the aligned form (bar.sync) does not allow.
+__device__ __forceinline__ void bar_workers() {
+  __syncwarp();
+  asm volatile("barrier.sync 1, %0;" ::"r"(kWorkers) : "memory");
+}
 
 // Add `inc` to the count of `key` (claiming a slot if new).  Returns false if no slot
 // was found within the probe limit.
@@ -1564,6 +1578,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
   uint32_t* hist = reinterpret_cast<uint32_t*>(sm + (size_t)cap_slots * (KW * 8 + 4));
   uint16_t* idx = reinterpret_cast<uint16_t*>(hist + padded_len(hist_max(KW)));  // [dcap]
   __shared__ uint64_t excl_s, next_s[3];  // next ticket, its input range
+  __shared__ volatile uint32_t ordered_s;  // the workers have ranked the current table
   __shared__ uint32_t next_u[2];          // its range-map interval: [next_u[0], next_u[1] - 1]
   __shared__ uint32_t ovf_s, special_s, nnew_s;
   __shared__ uint32_t wtmp[32];
@@ -1603,11 +1618,12 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     }
   };
   if (threadIdx.x == 0) {
+    ordered_s = 0;
     fetch_next(atomicAdd(ticket, 1ull));
     cp_async_wait_all();
   }
   while (true) {
-    __syncthreads();
+    block_sync();
     const uint64_t g = next_s[0];
     if (g >= NF) break;
     const uint64_t f0 = next_s[1];
@@ -1630,22 +1646,28 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     tb.counts = reinterpret_cast<uint32_t*>(tb.keys + (1u << bT));
     phase(7);
     table_clear<KW>(tb, 1u << bT);
-    __syncthreads();
+    block_sync();
     phase(0);
     count_all<KW>(tb, in, n, false, K(0), K(0), bT, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
-    __syncthreads();
+    block_sync();
     phase(1);
     const uint32_t dn = nnew_s;
     if (!ovf_s && dn <= dcap) {
       const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
-      if (threadIdx.x == 0) st_status(&b.look[g], (g == 0 ? kLookIncl : kLookAgg) | d);
-      // warp 0 resolves the exclusive prefix (look-back) while the workers order the table
+      if (threadIdx.x == 0) st_status(&b.look[g], (g == 0 && !s.defer_all ? kLookIncl : kLookAgg) | d);
+      // Warp 0 resolves the exclusive prefix (look-back) while the workers order the table,
+      // waiting on unpublished predecessors only as long as the workers are busy.  Without a
+      // prefix by then, the partition's run is written to its own input region instead
+      // (deferred) and k_compact moves it once all counts are known.
       uint32_t rank[kRankRegs];
       if (wid == 0) {
         const long long lb0 = clock64();
-        const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
+        const uint64_t ex = s.defer_all ? kNoPrefix : g == 0 ? 0 : lookback(b.look, g, &b.meta->status, &ordered_s);
         if (lane == 0) {
-          if (g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
+          const bool direct = ex != kNoPrefix;
+          if (direct && g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
+          b.fhist[g] = (uint32_t)d | (direct ? 0u : 0x80000000u);
+          if (!direct) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_deferred), 1ull);
           excl_s = ex;
           if (s.profile)
             atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[4]), (unsigned long long)(clock64() - lb0));
@@ -1668,17 +1690,27 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
                          prof);
         if (prof && threadIdx.x == 32) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
         rank_slots<KW>(tb, idx, idx, dn, hist, NB, lo, sh, big_s, big_n, rank, prof);
+        bar_workers();
+        if (threadIdx.x == 32) ordered_s = 1;
       }
-      __syncthreads();
+      block_sync();
       phase(3);
       const uint64_t ex = excl_s;
-      if (threadIdx.x == 0) fetch_next(atomicAdd(ticket, 1ull));
-      if (wid > 0) emit_slots<KW>(tb, idx, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+      if (threadIdx.x == 0) {
+        ordered_s = 0;
+        fetch_next(atomicAdd(ticket, 1ull));
+      }
+      // direct: final positions; deferred: the partition's own input region
+      const bool direct = ex != kNoPrefix;
+      uint64_t* okeys = direct ? b.out_keys : b.sbuf;
+      uint32_t* ocnts = direct ? b.out_counts : reinterpret_cast<uint32_t*>(b.kbuf);
+      const uint64_t obase = direct ? ex : f0, olim = direct ? s.cap : f0 + n;
+      if (wid > 0) emit_slots<KW>(tb, idx, dn, rank, obase, okeys, ocnts, olim, &b.meta->status);
       if (threadIdx.x == 0) {
         if (special_s) {
-          if (ex + dn < s.cap) {
-            store_key(b.out_keys, ex + dn, EMPTY);
-            b.out_counts[ex + dn] = special_s;
+          if (obase + dn < olim) {
+            store_key(okeys, obase + dn, EMPTY);
+            ocnts[obase + dn] = special_s;
           } else {
             atomicOr(&b.meta->status, ST_INTERNAL);
           }
@@ -1686,138 +1718,248 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
         cp_async_wait_all();
       }
       phase(5);
-      continue;  // the loop head synchronises
-    }
-    // ---------------- overflow path: too many distinct keys for the table.  Split the
-    // partition's key range into sub-ranges, each counted in its own table and ordered;
-    // the exclusive prefix is resolved first because the partial outputs are written
-    // before the total is known.  A sub-range narrower than the table holds fewer
-    // distinct keys than slots, so the splitting ends.
-    if (wid == 0) {
-      const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
-      if (lane == 0) excl_s = ex;
-    }
-    if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_overflow), 1ull);
-    K mn = EMPTY, mx = 0;
-    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      K key;
-      load_key(in, i, key);
-      if (key != EMPTY) {
-        mn = key < mn ? key : mn;
-        mx = key > mx ? key : mx;
+    } else {
+      // ---------------- overflow path: too many distinct keys for the table.  Split the
+      // partition's key range into sub-ranges, each counted in its own table and ordered;
+      // the exclusive prefix is resolved first because the partial outputs are written
+      // before the total is known.  A sub-range narrower than the table holds fewer
+      // distinct keys than slots, so the splitting ends.
+      if (wid == 0) {
+        const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status);
+        if (lane == 0) excl_s = ex;
       }
-    }
-    {
-      K a, c;
-      block_range<K>(mn, mx, red_lo, red_hi, a, c);
-      if (threadIdx.x == 0) {
-        stk_n = 0;
-        if (a <= c) {
-          stk_lo[0] = a;
-          stk_hi[0] = c;
-          stk_n = 1;
+      if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_overflow), 1ull);
+      K mn = EMPTY, mx = 0;
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        K key;
+        load_key(in, i, key);
+        if (key != EMPTY) {
+          mn = key < mn ? key : mn;
+          mx = key > mx ? key : mx;
         }
       }
-    }
-    __syncthreads();
-    const int bTf = s.bT_max;
-    tb.keys = reinterpret_cast<K*>(sm);
-    tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap_slots);
-    uint64_t written = 0;
-    while (stk_n > 0) {
-      const K lo = stk_lo[stk_n - 1], hi = stk_hi[stk_n - 1];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        --stk_n;
-        ovf_s = 0;
-        special_s = 0;
-        nnew_s = 0;
-      }
-      table_clear<KW>(tb, cap_slots);
-      __syncthreads();
-      count_all<KW>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
-      __syncthreads();
-      const uint32_t dn2 = nnew_s;
-      const K width = hi - lo;
-      if (ovf_s || dn2 > dcap) {
-        if (threadIdx.x == 0) {
-          if (width == 0 || stk_n + 2 > 160) {
-            atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
-          } else {
-            const K mid = lo + (width >> 1);
-            stk_lo[stk_n] = mid + 1;
-            stk_hi[stk_n] = hi;
-            stk_lo[stk_n + 1] = lo;
-            stk_hi[stk_n + 1] = mid;
-            stk_n += 2;
-          }
-        }
-        __syncthreads();
-        continue;
-      }
-      const uint64_t base = excl_s + written;
       {
-        uint32_t rank2[kRankRegs];
-        if (wid > 0) {
-          if (threadIdx.x == 32) {
-            range_s[0] = lo;
-            range_s[1] = hi;
+        K a, c;
+        block_range<K>(mn, mx, red_lo, red_hi, a, c);
+        if (threadIdx.x == 0) {
+          stk_n = 0;
+          if (a <= c) {
+            stk_lo[0] = a;
+            stk_hi[0] = c;
+            stk_n = 1;
           }
-          K lo2;
-          int sh2;
-          uint32_t NB2;
-          bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
-                           &b.meta->status);
-          rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
         }
-        __syncthreads();
-        if (wid > 0) emit_slots<KW>(tb, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
       }
-      written += dn2;
-      __syncthreads();
-    }
-    // the all-ones key, if present, is the largest key of all
-    uint32_t sp = 0;
-    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      K key;
-      load_key(in, i, key);
-      sp += key == EMPTY;
-    }
-#pragma unroll
-    for (int dd = 16; dd > 0; dd >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, dd);
-    if (lane == 0) wtmp[wid] = sp;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint64_t tot = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wtmp[w];
-      if (tot) {
-        if (tot > 0xffffffffull) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
-        if (excl_s + written < s.cap) {
-          store_key(b.out_keys, excl_s + written, EMPTY);
-          b.out_counts[excl_s + written] = (uint32_t)tot;
-        } else {
-          atomicOr(&b.meta->status, ST_INTERNAL);
+      block_sync();
+      const int bTf = s.bT_max;
+      tb.keys = reinterpret_cast<K*>(sm);
+      tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap_slots);
+      uint64_t written = 0;
+      while (stk_n > 0) {
+        const K lo = stk_lo[stk_n - 1], hi = stk_hi[stk_n - 1];
+        block_sync();
+        if (threadIdx.x == 0) {
+          --stk_n;
+          ovf_s = 0;
+          special_s = 0;
+          nnew_s = 0;
         }
-        ++written;
+        table_clear<KW>(tb, cap_slots);
+        block_sync();
+        count_all<KW>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+        block_sync();
+        const uint32_t dn2 = nnew_s;
+        const K width = hi - lo;
+        if (ovf_s || dn2 > dcap) {
+          if (threadIdx.x == 0) {
+            if (width == 0 || stk_n + 2 > 160) {
+              atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
+            } else {
+              const K mid = lo + (width >> 1);
+              stk_lo[stk_n] = mid + 1;
+              stk_hi[stk_n] = hi;
+              stk_lo[stk_n + 1] = lo;
+              stk_hi[stk_n + 1] = mid;
+              stk_n += 2;
+            }
+          }
+          block_sync();
+          continue;
+        }
+        const uint64_t base = excl_s + written;
+        {
+          uint32_t rank2[kRankRegs];
+          if (wid > 0) {
+            if (threadIdx.x == 32) {
+              range_s[0] = lo;
+              range_s[1] = hi;
+            }
+            K lo2;
+            int sh2;
+            uint32_t NB2;
+            bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
+                             &b.meta->status);
+            rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
+          }
+          block_sync();
+          if (wid > 0) emit_slots<KW>(tb, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+        }
+        written += dn2;
+        block_sync();
       }
-      st_status(&b.look[g], kLookIncl | (excl_s + written));
-      fetch_next(atomicAdd(ticket, 1ull));
-      cp_async_wait_all();
+      // the all-ones key, if present, is the largest key of all
+      uint32_t sp = 0;
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        K key;
+        load_key(in, i, key);
+        sp += key == EMPTY;
+      }
+  #pragma unroll
+      for (int dd = 16; dd > 0; dd >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, dd);
+      if (lane == 0) wtmp[wid] = sp;
+      block_sync();
+      if (threadIdx.x == 0) {
+        uint64_t tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wtmp[w];
+        if (tot) {
+          if (tot > 0xffffffffull) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
+          if (excl_s + written < s.cap) {
+            store_key(b.out_keys, excl_s + written, EMPTY);
+            b.out_counts[excl_s + written] = (uint32_t)tot;
+          } else {
+            atomicOr(&b.meta->status, ST_INTERNAL);
+          }
+          ++written;
+        }
+        st_status(&b.look[g], kLookIncl | (excl_s + written));
+        b.fhist[g] = (uint32_t)written;
+        fetch_next(atomicAdd(ticket, 1ull));
+        cp_async_wait_all();
+      }
+      phase(6);
     }
-    phase(6);
   }
 }
 
-// ------------------------------------------------------------------ final: distinct total
-__global__ void k_finish(Buffers b) {
-  const uint64_t NF = b.meta->n_fine;
-  if (NF == 0) {
-    b.meta->n_distinct = 0;
-    return;
+// ------------------------------------------------------------------ final: offsets of the runs
+// Exclusive scan of the distinct counts of the fine partitions (one block of 1024
+// threads): fcur[g] = first output position of partition g, n_distinct = the total.  The
+// look-back words are checked against it, and the deferred partitions are listed (in
+// increasing order) at the front of the spent look-back array for k_compact.
+__global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) {
+  __shared__ uint64_t wt[32];
+  __shared__ uint32_t wd[32];
+  __shared__ uint64_t carry_s;
+  __shared__ uint32_t dcarry_s;
+  const uint64_t NF = min(b.meta->n_fine, sh.nf_max);
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) {
+    carry_s = 0;
+    dcarry_s = 0;
   }
-  const unsigned long long v = ld_status(&b.look[NF - 1]);
-  if ((v >> 62) != 2) atomicOr(&b.meta->status, ST_INTERNAL);
-  b.meta->n_distinct = v & kLookValue;
+  __syncthreads();
+  bool bad = false;
+  for (uint64_t base = 0; base < NF; base += (uint64_t)nt * 8) {
+    uint32_t v[8];
+    unsigned long long lk[8];
+    uint64_t s = 0;
+    uint32_t nd = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint64_t i = base + (uint64_t)t * 8 + m;
+      v[m] = i < NF ? b.fhist[i] : 0;
+      lk[m] = i < NF ? ld_status(&b.look[i]) : 0;
+      s += v[m] & 0x7fffffffu;
+      nd += v[m] >> 31;
+    }
+    uint64_t x = s;
+    uint32_t y = nd;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t xs = __shfl_up_sync(0xffffffffu, x, d);
+      const uint32_t ys = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) {
+        x += xs;
+        y += ys;
+      }
+    }
+    if (lane == 31) {
+      wt[wid] = x;
+      wd[wid] = y;
+    }
+    __syncthreads();  // also: every look-back word of this chunk has been read
+    if (wid == 0) {
+      uint64_t w = wt[lane];
+      uint32_t z = wd[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t ws = __shfl_up_sync(0xffffffffu, w, d);
+        const uint32_t zs = __shfl_up_sync(0xffffffffu, z, d);
+        if (lane >= d) {
+          w += ws;
+          z += zs;
+        }
+      }
+      wt[lane] = w;
+      wd[lane] = z;
+    }
+    __syncthreads();
+    uint64_t run = carry_s + x - s + (wid ? wt[wid - 1] : 0);
+    uint32_t drun = dcarry_s + y - nd + (wid ? wd[wid - 1] : 0);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint64_t i = base + (uint64_t)t * 8 + m;
+      if (i < NF) {
+        const uint64_t d = v[m] & 0x7fffffffu;
+        const bool deferred = v[m] >> 31;
+        // a direct partition published its inclusive prefix, a deferred one its count
+        const uint64_t want = deferred ? (kLookAgg | d) : (kLookIncl | (run + d));
+        bad |= lk[m] != want;
+        b.fcur[i] = run;
+        if (deferred) b.look[drun++] = i;
+        run += d;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      carry_s += wt[31];
+      dcarry_s += wd[31];
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(&b.meta->status, ST_INTERNAL);
+  if (t == 0) {
+    b.meta->n_distinct = carry_s;
+    if (dcarry_s != b.meta->n_deferred) atomicOr(&b.meta->status, ST_INTERNAL);
+  }
+}
+
+// Move the runs of the deferred fine partitions from their input regions (keys in sbuf,
+// counts in kbuf as 32-bit words) to their output positions: one block per partition.
+template <int KW>
+__global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
+  typedef typename KeyT<KW>::T K;
+  const uint64_t n_def = b.meta->n_deferred;
+  const uint32_t* cnt_src = reinterpret_cast<const uint32_t*>(b.kbuf);
+  for (uint64_t q = blockIdx.x; q < n_def; q += gridDim.x) {
+    const uint64_t g = b.look[q];
+    if (g >= min(b.meta->n_fine, s.nf_max)) {
+      if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+      continue;
+    }
+    const uint32_t d = b.fhist[g] & 0x7fffffffu;
+    const uint64_t src = b.foff[g], dst = b.fcur[g];
+    if (src + d > s.cap || dst + d > s.cap) {
+      if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+      continue;
+    }
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+      K key;
+      load_key(b.sbuf, src + i, key);
+      store_key(b.out_keys, dst + i, key);
+      b.out_counts[dst + i] = cnt_src[src + i];
+    }
+  }
 }
 
 // ------------------------------------------------------------------ launches
@@ -1912,7 +2054,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
     ++launches;
     KC_STEP("k_scatter");
   }
-  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_log2, b.flo, P1, s.b1, s.fine_target, nf_max,
+  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_m, b.flo, P1, s.b1, s.fine_target, nf_max,
                                                b.meta);
   ++launches;
   KC_STEP("k_fine_plan");
@@ -1933,9 +2075,13 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   else k_count_emit<2><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
   ++launches;
   KC_STEP("k_count_emit");
-  k_finish<<<1, 1, 0, st>>>(b);
+  k_scan_distinct<<<1, 1024, 0, st>>>(s, b);
   ++launches;
-  KC_STEP("k_finish");
+  KC_STEP("k_scan_distinct");
+  if (s.kw == 1) k_compact<1><<<(unsigned)(n_sms * 8), 256, 0, st>>>(s, b);
+  else k_compact<2><<<(unsigned)(n_sms * 8), 256, 0, st>>>(s, b);
+  ++launches;
+  KC_STEP("k_compact");
   return launches;
 }
 

@@ -132,15 +132,16 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   const int P1 = 1 << s.b1;
   s.bT_max = kc::table_log2_max(s.kw, ds->smem_optin);
   s.tail = s.bT_max >= 10 ? 1024 : (1 << s.bT_max);
-  const double ft = (double)(1u << s.bT_max) * 0.5 * 0.75;
+  const double ft = (double)(1u << s.bT_max) * 0.55;
   s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
   s.cap = cap;
-  const uint64_t nf_bound = 2 * cap / s.fine_target + 3 * (uint64_t)P1 + 1;
-  const uint64_t nf_lim = (uint64_t)P1 << kc::kMaxFineLog2;
+  const uint64_t nf_bound = cap / s.fine_target + (uint64_t)P1 + 1;
+  const uint64_t nf_lim = (uint64_t)P1 * kc::kMaxFine;
   const uint32_t nf_max = (uint32_t)(nf_bound < nf_lim ? nf_bound : nf_lim);
   s.nf_max = nf_max;
   s.smem_budget = ds->smem_optin;
   s.profile = 0;
+  s.defer_all = 0;
 
   // scratch layout inside the static array
   size_t o = 0;
@@ -151,7 +152,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   };
   const size_t o_codes = take(s.n_words * 8), o_inv = take(s.n_words * 4), o_tf = take(s.n_tiles * 8);
   const size_t o_hist = take(s.n_tiles * P1 * 4), o_toff = take(s.n_tiles * P1 * 8);
-  const size_t o_cst = take((size_t)(P1 + 1) * 8), o_fb = take((size_t)(P1 + 1) * 4), o_fl = take((size_t)P1);
+  const size_t o_cst = take((size_t)(P1 + 1) * 8), o_fb = take((size_t)(P1 + 1) * 4), o_fl = take((size_t)P1 * 4);
   const size_t o_hll = take((size_t)kc::kHllRegs * 4);
   const size_t o_fh = take((size_t)nf_max * 4), o_fo = take((size_t)(nf_max + 1) * 8);
   const size_t o_flo = take((size_t)(nf_max + 1) * 4);
@@ -170,7 +171,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   b.toff = (uint64_t*)(ws + o_toff);
   b.cstart = (uint64_t*)(ws + o_cst);
   b.fine_base = (uint32_t*)(ws + o_fb);
-  b.fine_log2 = (uint8_t*)(ws + o_fl);
+  b.fine_m = (uint32_t*)(ws + o_fl);
   b.hll = (uint32_t*)(ws + o_hll);
   b.fhist = (uint32_t*)(ws + o_fh);
   b.foff = (uint64_t*)(ws + o_fo);

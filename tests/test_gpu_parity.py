@@ -188,6 +188,35 @@ def test_overflow_path_forced(torch_cuda):
         c.close()
 
 
+def test_deferred_write_out_forced(torch_cuda):
+    # every fine partition writes its run to its own input region and the compaction pass
+    # moves it to its place (the path of a partition whose output offset was not yet known)
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(defer_all=True)
+    try:
+        reads, offsets, _ = synth.generate(synth.REPEAT_SHORT, 1002, 0.003)
+        assert_parity(c, reads, offsets, 31, True, "deferred k31")
+        st = c.stats()
+        assert st["n_deferred_fine"] == st["n_fine"] - st["n_overflow_fine"] > 0
+        reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.002)
+        assert_parity(c, reads, offsets, 63, True, "deferred k63")
+        for k in (32, 64):  # the all-ones key, written last in its run
+            r, o = as_reads(["T" * 100, "ACGT" * 30, "T" * k, "GGT" + "T" * 70])
+            assert_parity(c, r, o, k, False, f"deferred all-T k={k}")
+    finally:
+        c.close()
+    # with tiny tables too: overflowing partitions (which wait for their offset) among
+    # deferred ones (which never publish an inclusive prefix)
+    c = KmerCounter(defer_all=True, table_slots_max=64)
+    try:
+        reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.02)
+        assert_parity(c, reads, offsets, 31, True, "deferred + overflow k31")
+        st = c.stats()
+        assert st["n_overflow_fine"] > 0 and st["n_deferred_fine"] > 0
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("hint", [1, 4096])
 def test_partition_count_extremes(torch_cuda, hint):
     from paper_2505_04431_gb300 import KmerCounter
