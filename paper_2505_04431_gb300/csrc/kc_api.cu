@@ -284,8 +284,10 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   int b1;
   if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
   else {
-    // about 8 MB of keys per coarse partition, at most 2048 partitions
-    const int want = ceil_log2_u64((L * (uint64_t)(k <= 32 ? 1 : 2)) / (1u << 20) + 1);
+    // coarse partitions of at most about 6 M windows: few enough partitions that the keys
+    // pass B writes for one partition per step form runs of whole sectors, small enough
+    // that a partition of distinct keys splits into at most ~1400 fine partitions
+    const int want = ceil_log2_u64(L / (6u << 20) + 1);
     b1 = want < 11 ? want : 11;
   }
   s.b1 = b1;

@@ -22,11 +22,11 @@ constexpr int kTileWords = 8192;               // one phase-1 tile = 262144 base
 constexpr uint64_t kTileBases = (uint64_t)kTileWords * kWordBases;
 constexpr int kPackThreads = 512;              // pass A: one code word per thread per sub-step
 constexpr int kMaxCoarseLog2 = 12;             // at most 4096 coarse partitions
-constexpr int kMaxFine = 1024;                 // at most this many fine partitions per coarse one
+constexpr int kMaxFine = 2048;                 // at most this many fine partitions per coarse one
 constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
 constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
 constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
-constexpr int kFineLocalCap = 1024;            // fine partitions one chunk may span (shared histogram)
+constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
 constexpr int kHllLog2 = 10;                   // distinct-key sketch: 1024 registers
 constexpr int kHllRegs = 1 << kHllLog2;
 constexpr int kHllSampleLog2 = 3;              // ... over a 1/8 hash sample of the keys

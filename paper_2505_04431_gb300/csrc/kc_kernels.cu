@@ -645,14 +645,20 @@ __global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_
   }
   __syncthreads();
   const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1, wt);
-  for (int c = threadIdx.x; c < P1; c += blockDim.x) {
-    fine_base[c] = (uint32_t)fsc[c];
-    // fine partition fine_base[c] + f holds the values u of coarse field c whose low part
-    // v = u mod 2^(32 - b1) has floor(v m / 2^(32 - b1)) = f, i.e. v >= ceil(f 2^(32 - b1) / m)
-    const uint64_t m = fine_m[c], w = 1ull << (32 - b1);
-    const uint32_t u0 = (uint32_t)((uint64_t)c << (32 - b1));
-    for (uint64_t f = 0; f < m; ++f)
-      if (fsc[c] + f < nf_max) flo[fsc[c] + f] = u0 + (uint32_t)((f * w + m - 1) / m);
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) fine_base[c] = (uint32_t)fsc[c];
+  // fine partition g = fsc[c] + f holds the values u of coarse field c whose low part
+  // v = u mod 2^(32 - b1) has floor(v m / 2^(32 - b1)) = f, i.e. v >= ceil(f 2^(32 - b1) / m);
+  // one thread per fine partition, its coarse partition found by binary search in fsc
+  const uint64_t w = 1ull << (32 - b1);
+  for (uint64_t g = threadIdx.x; g < NF && g < nf_max; g += blockDim.x) {
+    int lo = 0, hi = P1 - 1;  // last c with fsc[c] <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (fsc[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint64_t m = fine_m[lo], f = g - fsc[lo];
+    flo[g] = (uint32_t)((uint64_t)lo << (32 - b1)) + (uint32_t)((f * w + m - 1) / m);
   }
   if (threadIdx.x == 0) {
     if (NF <= nf_max) flo[NF] = 0;  // so that the last partition ends at u = 2^32 - 1
