@@ -679,7 +679,10 @@ __device__ __forceinline__ uint64_t key_hash(u128 key) {
   return ((uint64_t)key ^ ((uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
 }
 
-template <int KW, int NT>
+// KEEP_C: each window's coarse partition is kept in shared memory (taken in phase 1,
+// carried to the staging and the write-out) instead of being recomputed from the key
+// twice; used when two blocks per SM still fit.
+template <int KW, int NT, bool KEEP_C>
 __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
   constexpr int WPT = KW == 1 ? 32 : 16;    // windows per thread
@@ -692,6 +695,8 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   unsigned long long* cursor = reinterpret_cast<unsigned long long*>(stage + SUB);   // [P1] absolute write positions
   uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);                            // [padded P1]
   uint32_t* soff = hist + padded_len(P1);                                               // [padded P1]
+  uint16_t* rawc = reinterpret_cast<uint16_t*>(soff + padded_len(P1));  // KEEP_C: [SUB], window i of thread t at i * NT + t
+  uint16_t* stage_c = rawc + SUB;                                        // KEEP_C: [SUB], partition of each staged key
   __shared__ uint64_t code_s[NW + 2];
   __shared__ uint32_t inv_s[NW + 2];
   __shared__ uint32_t st_s[NW + 2];
@@ -745,21 +750,24 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
       const uint32_t vm = valid_mask(inv_s[sw - 2], inv_s[sw - 1], inv_s[sw], st_s[sw - 2], st_s[sw - 1], st_s[sw], s.k);
       win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], vm, h, s.k, W);
       valid = W.valid & (WPT == 32 ? 0xffffffffu : 0xffffu);
+      // the arithmetic of every window is branch-free (so that the windows' dependency chains
+      // interleave); only the shared-memory updates depend on the window being valid
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
-        if ((valid >> i) & 1u) {
-          uint64_t c0, c1;
-          win_top<KW, WPT>(W, i, s.canonical, c0, c1);
-          top_to_key(c0, c1, s.k, keys[i]);
-          const uint32_t c = coarse_field(umap((uint32_t)(c0 >> 32), s.canonical), s.b1);
-          const uint32_t r = atomicAdd(&hist[PAD(c)], 1u);
-          rr[i >> 1] |= r << (16 * (i & 1));
-          const uint64_t hh = key_hash(keys[i]);
-          if ((hh >> (64 - kHllSampleLog2)) == 0) {
-            const uint32_t reg = (uint32_t)(hh >> (64 - kHllSampleLog2 - kHllLog2)) & (kHllRegs - 1);
-            const uint64_t rest = hh << (kHllSampleLog2 + kHllLog2);
-            atomicMax(&hll_s[reg], (uint32_t)min(__clzll(rest) + 1, 64 - kHllSampleLog2 - kHllLog2 + 1));
-          }
+        uint64_t c0, c1;
+        win_top<KW, WPT>(W, i, s.canonical, c0, c1);
+        top_to_key(c0, c1, s.k, keys[i]);
+        const uint32_t c = coarse_field(umap((uint32_t)(c0 >> 32), s.canonical), s.b1);
+        const uint64_t hh = key_hash(keys[i]);
+        const bool v = (valid >> i) & 1u;
+        if (v) {
+          if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
+          rr[i >> 1] |= atomicAdd(&hist[PAD(c)], 1u) << (16 * (i & 1));
+        }
+        if (v && (hh >> (64 - kHllSampleLog2)) == 0) {
+          const uint32_t reg = (uint32_t)(hh >> (64 - kHllSampleLog2 - kHllLog2)) & (kHllRegs - 1);
+          const uint64_t rest = hh << (kHllSampleLog2 + kHllLog2);
+          atomicMax(&hll_s[reg], (uint32_t)min(__clzll(rest) + 1, 64 - kHllSampleLog2 - kHllLog2 + 1));
         }
       }
     }
@@ -770,9 +778,12 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
 #pragma unroll
     for (int i = 0; i < WPT; ++i) {
       if (valid & (1u << i)) {
-        const uint32_t c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
+        uint32_t c;
+        if constexpr (KEEP_C) c = rawc[i * NT + t];
+        else c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
         const uint32_t pos = soff[PAD(c)] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
         stage[pos] = keys[i];
+        if constexpr (KEEP_C) stage_c[pos] = (uint16_t)c;
       }
     }
     __syncthreads();
@@ -783,7 +794,10 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
     __syncthreads();
     for (uint32_t i = t; i < n_sub; i += NT) {
       const K key = stage[i];
-      const uint64_t pos = cursor[coarse_of(key, s.k, s.canonical, s.b1)] + i;  // runs are grouped by partition
+      uint32_t c;
+      if constexpr (KEEP_C) c = stage_c[i];
+      else c = coarse_of(key, s.k, s.canonical, s.b1);  // runs are grouped by partition
+      const uint64_t pos = cursor[c] + i;
       if (pos < s.cap) store_key(b.kbuf, pos, key);
       else atomicOr(&b.meta->status, ST_INTERNAL);
     }
@@ -1969,9 +1983,9 @@ __global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
 }
 
 // ------------------------------------------------------------------ launches
-static size_t scatter_smem(int kw, int nt, int P1) {
+static size_t scatter_smem(int kw, int nt, int P1, bool keep_c) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
-  return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4;
+  return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4 + (keep_c ? sub * 4 : 0);
 }
 static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 8 + kFineLocalCap * 4 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
@@ -1993,8 +2007,10 @@ int configure_kernels(int device) {
   }
   KC_SET(k_pack_count<1>);
   KC_SET(k_pack_count<2>);
-  KC_SET((k_scatter<1, 256>));
-  KC_SET((k_scatter<2, 256>));
+  KC_SET((k_scatter<1, 256, false>));
+  KC_SET((k_scatter<2, 256, false>));
+  KC_SET((k_scatter<1, 256, true>));
+  KC_SET((k_scatter<2, 256, true>));
   KC_SET(k_fine_plan);
   KC_SET(k_fine_hist<1>);
   KC_SET(k_fine_hist<2>);
@@ -2052,11 +2068,21 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   ++launches;
   KC_STEP("k_bucket_scan");
   if (s.n_tiles > 0) {
-    const size_t smB = scatter_smem(s.kw, 256, P1);
+    const size_t smB = scatter_smem(s.kw, 256, P1, false), smK = scatter_smem(s.kw, 256, P1, true);
     if (smB + 8704 > s.smem_budget) return -(int)cudaErrorInvalidConfiguration;
+    // keep each window's coarse partition in shared memory if two blocks per SM still fit
+    int per_sm = 0;
+    if (s.kw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<1, 256, true>, 256, smK);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<2, 256, true>, 256, smK);
+    const bool keep_c = per_sm >= 2;
     const unsigned gt = (unsigned)s.n_tiles;
-    if (s.kw == 1) k_scatter<1, 256><<<gt, 256, smB, st>>>(s, b);
-    else k_scatter<2, 256><<<gt, 256, smB, st>>>(s, b);
+    if (s.kw == 1) {
+      if (keep_c) k_scatter<1, 256, true><<<gt, 256, smK, st>>>(s, b);
+      else k_scatter<1, 256, false><<<gt, 256, smB, st>>>(s, b);
+    } else {
+      if (keep_c) k_scatter<2, 256, true><<<gt, 256, smK, st>>>(s, b);
+      else k_scatter<2, 256, false><<<gt, 256, smB, st>>>(s, b);
+    }
     ++launches;
     KC_STEP("k_scatter");
   }
