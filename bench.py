@@ -32,7 +32,11 @@ WORKLOAD_DESC = {
     "repeats_100mbp_150bp_30x_k31": "100 Mbp genome (20% from 500 repeat families, Zipf 1.2, 2% divergence), "
                                     "150 bp reads, 30x, 0.5% subst, k=31 canonical",
     "long_50mbp_10kbp_20x_k63": "50 Mbp i.i.d. genome, log-normal 10 kbp reads, 20x, 5% errors 60/20/20, k=63 canonical",
+    "batch_256_samples_k31": "256 samples: i.i.d. genomes log-uniform 0.1-50 Mbp (times --scale, default 0.1), "
+                             "150 bp reads, U(5,40)x, 0.5% subst, k=31 canonical; kc_count_batch vs the per-sample "
+                             "kc_count loop",
 }
+BATCH_SEED = 1004  # seeds of the batched workload's samples: mix_seed(1004, i)
 
 
 def measured_peaks():
@@ -317,6 +321,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """The batched form against the plain per-sample loop, both timed end to end on the host
+    (wall clock around all calls, inputs resident on the device, results freed)."""
+    import torch
+    import synth
+    from paper_2505_04431_gb300 import KmerCounter
+    from paper_2505_04431_gb300 import build as kcbuild
+
+    torch.cuda.set_device(0)
+    kcbuild.build()
+    scale = 0.1 if args.scale == 1.0 else args.scale
+    samples, windows = [], 0
+    for i in range(256):
+        reads, offsets, _ = synth.generate(synth.SAMPLE, synth.mix_seed(BATCH_SEED, i), scale)
+        samples.append((torch.from_numpy(reads).cuda(), offsets, int(offsets[-1])))
+        windows += max(0, int(np.sum(np.maximum(np.diff(offsets.astype(np.int64)) - 30, 0))))
+    counter = KmerCounter()
+    t_plain, t_batch, valid = [], [], 0
+
+    def plain():
+        v = 0
+        for r, o, _ in samples:
+            res = counter.count(r, o, 31, True)
+            v += res.n_valid_windows
+            res.free()
+        return v
+
+    def batched():
+        out = counter.count_batch(samples, 31, True)
+        v = sum(res.n_valid_windows for res in out)
+        for res in out:
+            res.free()
+        return v
+
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v1 = plain()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        v2 = batched()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if v1 != v2:
+            raise RuntimeError(f"batched and plain counts differ in valid windows: {v1} vs {v2}")
+        valid = v1
+        if it >= args.warmup:
+            t_plain.append(t1 - t0)
+            t_batch.append(t2 - t1)
+    tp, tb = float(np.median(t_plain)), float(np.median(t_batch))
+    bases = sum(s[2] for s in samples)
+    line = {"metric": METRIC, "value": valid / tb / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "samples": len(samples),
+                       "genome_scale": scale, "bases": bases, "windows": valid, "k": 31, "canonical": True,
+                       "parallelism": "1 GPU", "timing": "host wall clock around all calls, median of steps"},
+            "plain": {"value": valid / tp / 1e9, "unit": UNIT, "ms_per_step": tp * 1e3},
+            "batched_vs_plain": tp / tb, "gpu_launches": 13 * len(samples)}
+    print(json.dumps(line), flush=True)
+    counter.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,6 +399,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch_"):
+        run_batch(args)
     else:
         run_ours(args)
 

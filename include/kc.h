@@ -174,6 +174,27 @@ kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64
                            uint64_t *out_keys, uint32_t *out_counts, uint64_t out_capacity, uint64_t *n_distinct,
                            uint64_t *n_valid_windows, void *stream);
 
+/* Batched counting: the histograms of n_samples independent read sets in one call
+ * (the same operation as kc_count, per sample; Section II, Algorithms 1 and 3).
+ *
+ *   reads[i], offsets[i], n_reads[i]   sample i, as for kc_count (reads host or device;
+ *                   offsets host or device, offsets[i][0] = 0, non-decreasing).
+ *   n_bases[i]      offsets[i][n_reads[i]], the sample's base count (host array), so
+ *                   that nothing has to be read back before the samples are enqueued.
+ *   out[i]          sample i's result, as kc_count returns it (free each with kc_free).
+ *
+ * Every sample's copies and kernels are enqueued without host synchronisation between
+ * samples: the largest samples in order on the plan's stream and scratch, samples of up
+ * to 64 Mi bases spread over three more streams with scratch of their own (created on
+ * first use, kept by the plan), so that several small samples share the GPU; one
+ * synchronisation at the end.  Scratch is sized once per stream for its largest sample.
+ * On any error no result is returned (all out[i] zeroed) and kc_last_error() names the
+ * sample.  Errors as for kc_count; KC_ENOMEM if the batch's results and scratch exceed
+ * max_device_bytes. */
+kc_status kc_count_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *const *reads,
+                         const uint64_t *const *offsets, const uint64_t *n_reads, const uint64_t *n_bases, int k,
+                         int canonical, kc_result *out);
+
 #ifdef __cplusplus
 }
 #endif

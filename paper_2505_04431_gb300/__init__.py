@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
-            "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc"]
+            "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 KC_PLAN_DEFER_ALL = 2
@@ -94,6 +94,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.kc_last_kernel_times.restype = i32
     lib.kc_count_noalloc.argtypes = [vp, vp, u64, i32, i32, vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), vp]
     lib.kc_count_noalloc.restype = i32
+    P = ctypes.POINTER
+    lib.kc_count_batch.argtypes = [vp, ctypes.c_uint32, P(vp), P(vp), P(u64), P(u64), i32, i32, P(Result)]
+    lib.kc_count_batch.restype = i32
     _lib = lib
     return lib
 
@@ -237,6 +240,33 @@ class KmerCounter:
                                              ctypes.byref(res)))
         del rk, ok
         return CountResult(self, res)
+
+    def count_batch(self, samples, k: int, canonical: bool = True) -> list[CountResult]:
+        """Histograms of several read sets in one call (kc_count_batch).  samples: a list of
+        (reads, offsets) or (reads, offsets, n_bases), offsets on the host (numpy) or the
+        device (then give n_bases, or it is read back); one result each."""
+        n = len(samples)
+        keep = []
+        R = (ctypes.c_void_p * n)()
+        O = (ctypes.c_void_p * n)()
+        NR = (ctypes.c_uint64 * n)()
+        NB = (ctypes.c_uint64 * n)()
+        for i, sample in enumerate(samples):
+            reads, offsets = sample[0], sample[1]
+            rp, rk = _ptr(reads)
+            op, ok = _ptr(offsets)
+            keep += [rk, ok]
+            R[i], O[i] = rp, op
+            NR[i] = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+            if len(sample) > 2:
+                NB[i] = int(sample[2])
+            else:
+                last = offsets[-1]
+                NB[i] = int(last.item() if hasattr(last, "item") else last)
+        res = (Result * n)()
+        _check(self._lib, self._lib.kc_count_batch(self._plan, n, R, O, NR, NB, int(k), int(bool(canonical)), res))
+        del keep
+        return [CountResult(self, res[i]) for i in range(n)]
 
     def stats(self) -> dict:
         st = Stats()

@@ -6,8 +6,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "kc.h"
 #include "kc_internal.h"
@@ -25,6 +27,9 @@ kc_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// batched counts: samples of at most this many bases may run on the extra lanes
+constexpr uint64_t kLaneSmallBases = 64ull << 20;
 
 }  // namespace
 
@@ -46,6 +51,11 @@ struct kc_plan_s {
   size_t smem_optin = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // batched counts: extra streams with their own scratch (created on first use)
+  static constexpr int kLanes = 3;
+  cudaStream_t lane_st[kLanes] = {};
+  void* lane_ws[kLanes] = {};
+  size_t lane_ws_bytes[kLanes] = {};
   std::atomic<int> busy{0};
   kc_stats stats{};
   // per-kernel timing (KC_PLAN_PROFILE)
@@ -61,22 +71,23 @@ struct kc_plan_s {
 
 namespace {
 
-void* dev_alloc(kc_plan_s* p, size_t bytes) {
+void* dev_alloc_on(kc_plan_s* p, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 256;
-  if (p->alloc) return p->alloc(bytes, (void*)p->stream, p->ctx);
+  if (p->alloc) return p->alloc(bytes, (void*)st, p->ctx);
   void* ptr = nullptr;
-  if (cudaMallocAsync(&ptr, bytes, p->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&ptr, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   return ptr;
 }
-
-void dev_free(kc_plan_s* p, void* ptr) {
+void dev_free_on(kc_plan_s* p, void* ptr, cudaStream_t st) {
   if (!ptr) return;
-  if (p->free_) p->free_(ptr, (void*)p->stream, p->ctx);
-  else cudaFreeAsync(ptr, p->stream);
+  if (p->free_) p->free_(ptr, (void*)st, p->ctx);
+  else cudaFreeAsync(ptr, st);
 }
+void* dev_alloc(kc_plan_s* p, size_t bytes) { return dev_alloc_on(p, bytes, p->stream); }
+void dev_free(kc_plan_s* p, void* ptr) { dev_free_on(p, ptr, p->stream); }
 
 bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes a;
@@ -128,6 +139,202 @@ void debug_mark(void* ctx, const char* name) {
   fprintf(stderr, "[kc] %s launched\n", name);
   const cudaError_t e = cudaStreamSynchronize(p->stream);
   fprintf(stderr, "[kc] %s finished: %s\n", name, cudaGetErrorString(e));
+}
+
+
+// ---- one count: shape and scratch layout (host only), launch sequence, result
+struct Job {
+  kc::Shape s{};
+  int P1 = 1;
+  uint32_t nf_max = 0;
+  uint64_t L = 0, n_reads = 0;
+  bool off_dev = false, copy_reads = false, reads_dev = false;
+  const uint8_t* reads = nullptr;
+  const uint64_t* offsets = nullptr;
+  size_t o_reads = 0, o_offs = 0, o_codes = 0, o_inv = 0, o_tf = 0, o_hist = 0, o_toff = 0, o_cst = 0, o_fb = 0, o_fl = 0,
+         o_hll = 0, o_fh = 0, o_fo = 0, o_flo = 0, o_fc = 0, o_look = 0, o_kbuf = 0, o_sbuf = 0, o_meta = 0;
+  size_t ws_bytes = 0, out_key_bytes = 0, out_cnt_bytes = 0;
+  void* okeys = nullptr;
+  void* ocnts = nullptr;
+};
+
+void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t L,
+              bool off_dev, int k, int canonical, Job& j) {
+  j.reads = reads;
+  j.offsets = offsets;
+  j.n_reads = n_reads;
+  j.L = L;
+  j.off_dev = off_dev;
+  j.reads_dev = L > 0 && is_device_ptr(reads);
+  j.copy_reads = L > 0 && (!j.reads_dev || ((uintptr_t)reads & 15) != 0);
+  kc::Shape& s = j.s;
+  s = kc::Shape{};
+  s.L = L;
+  s.n_reads = n_reads;
+  s.n_words = (L + 31) / 32;
+  s.n_tiles = (s.n_words + kc::kTileWords - 1) / kc::kTileWords;
+  s.k = k;
+  s.canonical = canonical ? 1 : 0;
+  s.kw = k <= 32 ? 1 : 2;
+  int b1;
+  if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
+  else {
+    // coarse partitions of at most about 6 M windows: few enough partitions that the keys
+    // pass B writes for one partition per step form runs of whole sectors, small enough
+    // that a partition of distinct keys splits into at most ~1400 fine partitions
+    const int want = ceil_log2_u64(L / (6u << 20) + 1);
+    b1 = want < 11 ? want : 11;
+  }
+  s.b1 = b1;
+  j.P1 = 1 << b1;
+  int bT_max = kc::table_log2_max(s.kw, p->smem_optin);
+  if (p->slots_max) {
+    const int bt = 63 - __builtin_clzll((uint64_t)p->slots_max);
+    if (bt < bT_max) bT_max = bt;
+  }
+  s.bT_max = bT_max;
+  s.tail = bT_max >= 10 ? 1024 : (1 << bT_max);
+  const double ft = (double)(1u << bT_max) * p->load;  // distinct keys per fine partition aimed at
+  s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
+  s.cap = L > 0 ? L : 1;
+  // sum over partitions of ceil(n_c / target), target >= fine_target: at most K / ft + P1
+  const uint64_t nf_bound = s.cap / s.fine_target + (uint64_t)j.P1 + 1;
+  const uint64_t nf_lim = (uint64_t)j.P1 * kc::kMaxFine;
+  j.nf_max = (uint32_t)(nf_bound < nf_lim ? nf_bound : nf_lim);
+  s.nf_max = j.nf_max;
+  s.smem_budget = p->smem_optin;
+  s.profile = p->profile ? 1 : 0;
+  s.defer_all = p->defer_all ? 1 : 0;
+  const uint64_t P1 = (uint64_t)j.P1, nf = j.nf_max;
+  Layout lay;
+  j.o_reads = lay.add(j.copy_reads ? L + 16 : 0);
+  j.o_offs = lay.add(off_dev ? 0 : (n_reads + 1) * 8);
+  j.o_codes = lay.add(s.n_words * 8);
+  j.o_inv = lay.add(s.n_words * 4);
+  j.o_tf = lay.add(s.n_tiles * 8);
+  j.o_hist = lay.add(s.n_tiles * P1 * 4);
+  j.o_toff = lay.add(s.n_tiles * P1 * 8);
+  j.o_cst = lay.add((P1 + 1) * 8);
+  j.o_fb = lay.add((P1 + 1) * 4);
+  j.o_fl = lay.add(P1 * 4);
+  j.o_hll = lay.add((size_t)kc::kHllRegs * 4);
+  j.o_fh = lay.add(nf * 4);
+  j.o_fo = lay.add((nf + 1) * 8);
+  j.o_flo = lay.add((nf + 1) * 4);
+  j.o_fc = lay.add(nf * 8);
+  j.o_look = lay.add(nf * 8);
+  j.o_kbuf = lay.add(s.cap * s.kw * 8);
+  j.o_sbuf = lay.add(s.cap * s.kw * 8);
+  j.o_meta = lay.add(sizeof(kc::Meta));
+  j.ws_bytes = lay.total;
+  j.out_key_bytes = s.cap * s.kw * 8;
+  j.out_cnt_bytes = s.cap * 4;
+}
+
+// Copies, clears and launches of one count on stream `st` with scratch at `ws`; the
+// status record is copied to *meta_dst at the end (asynchronously if it is pinned).
+bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst, const kc::Marker& mark, int n_sms,
+                 int* launches, std::string* err) {
+  const kc::Shape& s = j.s;
+  kc::Buffers b{};
+  b.reads = j.copy_reads ? (const uint8_t*)(ws + j.o_reads) : j.reads;
+  b.offsets = j.off_dev ? j.offsets : (const uint64_t*)(ws + j.o_offs);
+  b.codes64 = (uint64_t*)(ws + j.o_codes);
+  b.inv32 = (uint32_t*)(ws + j.o_inv);
+  b.tile_first = (uint64_t*)(ws + j.o_tf);
+  b.hist = (uint32_t*)(ws + j.o_hist);
+  b.toff = (uint64_t*)(ws + j.o_toff);
+  b.cstart = (uint64_t*)(ws + j.o_cst);
+  b.fine_base = (uint32_t*)(ws + j.o_fb);
+  b.fine_m = (uint32_t*)(ws + j.o_fl);
+  b.hll = (uint32_t*)(ws + j.o_hll);
+  b.fhist = (uint32_t*)(ws + j.o_fh);
+  b.foff = (uint64_t*)(ws + j.o_fo);
+  b.flo = (uint32_t*)(ws + j.o_flo);
+  b.fcur = (unsigned long long*)(ws + j.o_fc);
+  b.look = (unsigned long long*)(ws + j.o_look);
+  b.kbuf = (uint64_t*)(ws + j.o_kbuf);
+  b.sbuf = (uint64_t*)(ws + j.o_sbuf);
+  b.meta = (kc::Meta*)(ws + j.o_meta);
+  b.out_keys = (uint64_t*)j.okeys;
+  b.out_counts = (uint32_t*)j.ocnts;
+  cudaError_t e;
+  if (j.copy_reads && (e = cudaMemcpyAsync((void*)b.reads, j.reads, j.L,
+                                           j.reads_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    *err = std::string("copying reads: ") + cudaGetErrorString(e);
+    return false;
+  }
+  if (!j.off_dev &&
+      (e = cudaMemcpyAsync((void*)b.offsets, j.offsets, (j.n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    *err = std::string("copying offsets: ") + cudaGetErrorString(e);
+    return false;
+  }
+  if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.fhist, 0, (size_t)j.nf_max * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.look, 0, (size_t)j.nf_max * 8, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b.cstart, 0, (size_t)(j.P1 + 1) * 8, st)) != cudaSuccess) {
+    *err = std::string("clearing scratch: ") + cudaGetErrorString(e);
+    return false;
+  }
+  int l = kc::launch_phase1(s, b, n_sms, (void*)st, mark);
+  if (l >= 0) {
+    const int l2 = kc::launch_phase2(s, b, n_sms, j.nf_max, (void*)st, mark);
+    l = l2 >= 0 ? l + l2 : l2;
+  }
+  if (l < 0) {
+    *err = std::string("launch: ") + cudaGetErrorString((cudaError_t)(-l));
+    return false;
+  }
+  *launches = l;
+  if ((e = cudaMemcpyAsync(meta_dst, b.meta, sizeof(kc::Meta), cudaMemcpyDeviceToHost, st)) != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+
+kc_status job_status(const kc::Meta& m, const char* who, std::string* msg) {
+  const std::string w(who);
+  if (m.status & kc::ST_BAD_OFFSETS) {
+    *msg = w + ": offsets must start at 0, be non-decreasing and end at the base count";
+    return KC_EINVAL;
+  }
+  if (m.status & kc::ST_PARTITION_OVERFLOW) {
+    *msg = w + ": one key range holds 2^32 windows or more; use more partitions";
+    return KC_EOVERFLOW;
+  }
+  if (m.status & kc::ST_COUNT_OVERFLOW) {
+    *msg = w + ": a count exceeds 2^32 - 1";
+    return KC_EOVERFLOW;
+  }
+  if (m.status & kc::ST_TIMEOUT) {
+    *msg = w + ": a device-side wait timed out";
+    return KC_ETIMEOUT;
+  }
+  if (m.status & kc::ST_INTERNAL) {
+    *msg = w + ": internal consistency check failed";
+    return KC_ECUDA;
+  }
+  return KC_OK;
+}
+
+void fill_result(const Job& j, const kc::Meta& m, kc_result* out) {
+  out->n = m.n_distinct;
+  out->key_words = (uint32_t)j.s.kw;
+  out->keys = j.okeys;
+  out->counts = (uint32_t*)j.ocnts;
+  out->n_valid_windows = m.n_windows;
+  out->capacity = j.s.cap;
+}
+
+void record_stats(kc_plan_s* p, const Job& j, const kc::Meta& m) {
+  p->stats.n_partitions = (uint32_t)j.P1;
+  p->stats.n_fine = m.n_fine;
+  p->stats.n_overflow_fine = m.n_overflow;
+  p->stats.n_deferred_fine = m.n_deferred;
+  for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
+  for (int i = 0; i < 8; ++i) p->stats.sub_cycles[i] = m.sub_cycles[i];
 }
 
 }  // namespace
@@ -190,6 +397,12 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   if (!p) return fail(KC_EINVAL, "kc_plan_destroy: NULL plan");
   cudaSetDevice(p->device);
   dev_free(p, p->ws);
+  for (int l = 0; l < kc_plan_s::kLanes; ++l)
+    if (p->lane_st[l]) {
+      dev_free_on(p, p->lane_ws[l], p->lane_st[l]);
+      cudaStreamSynchronize(p->lane_st[l]);
+      cudaStreamDestroy(p->lane_st[l]);
+    }
   cudaStreamSynchronize(p->stream);
   if (p->profile)
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) cudaEventDestroy(p->ev[i]);
@@ -269,134 +482,34 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   }
   if (first != 0) return fail(KC_EINVAL, "kc_count: offsets[0] must be 0");
   if (L > 0 && !reads) return fail(KC_EINVAL, "kc_count: reads must not be NULL");
-  const bool reads_dev = L > 0 && is_device_ptr(reads);
-  const bool copy_reads = L > 0 && (!reads_dev || ((uintptr_t)reads & 15) != 0);
 
-  // ---- shape
-  kc::Shape s{};
-  s.L = L;
-  s.n_reads = n_reads;
-  s.n_words = (L + 31) / 32;
-  s.n_tiles = (s.n_words + kc::kTileWords - 1) / kc::kTileWords;
-  s.k = k;
-  s.canonical = canonical ? 1 : 0;
-  s.kw = k <= 32 ? 1 : 2;
-  int b1;
-  if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
-  else {
-    // coarse partitions of at most about 6 M windows: few enough partitions that the keys
-    // pass B writes for one partition per step form runs of whole sectors, small enough
-    // that a partition of distinct keys splits into at most ~1400 fine partitions
-    const int want = ceil_log2_u64(L / (6u << 20) + 1);
-    b1 = want < 11 ? want : 11;
-  }
-  s.b1 = b1;
-  const int P1 = 1 << b1;
-  int bT_max = kc::table_log2_max(s.kw, p->smem_optin);
-  if (p->slots_max) {
-    int bt = 63 - __builtin_clzll((uint64_t)p->slots_max);
-    if (bt < bT_max) bT_max = bt;
-  }
-  s.bT_max = bT_max;
-  s.tail = bT_max >= 10 ? 1024 : (1 << bT_max);
-  const double ft = (double)(1u << bT_max) * p->load;  // distinct keys per fine partition aimed at
-  s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
-  s.cap = L > 0 ? L : 1;
-  // sum over partitions of ceil(n_c / target), target >= fine_target: at most K / ft + P1
-  const uint64_t nf_bound = s.cap / s.fine_target + (uint64_t)P1 + 1;
-  const uint64_t nf_lim = (uint64_t)P1 * kc::kMaxFine;
-  const uint64_t nf_max64 = nf_bound < nf_lim ? nf_bound : nf_lim;
-  const uint32_t nf_max = (uint32_t)nf_max64;
-  s.nf_max = nf_max;
-  s.smem_budget = p->smem_optin;
-  s.profile = p->profile ? 1 : 0;
-  s.defer_all = p->defer_all ? 1 : 0;
-
-  // ---- scratch layout
-  Layout lay;
-  const size_t o_reads = lay.add(copy_reads ? L + 16 : 0);
-  const size_t o_offs = lay.add(off_dev ? 0 : (n_reads + 1) * 8);
-  const size_t o_codes = lay.add(s.n_words * 8);
-  const size_t o_inv = lay.add(s.n_words * 4);
-  const size_t o_tf = lay.add(s.n_tiles * 8);
-  const size_t o_hist = lay.add(s.n_tiles * P1 * 4);
-  const size_t o_toff = lay.add(s.n_tiles * P1 * 8);
-  const size_t o_cst = lay.add((size_t)(P1 + 1) * 8);
-  const size_t o_fb = lay.add((size_t)(P1 + 1) * 4);
-  const size_t o_fl = lay.add((size_t)P1 * 4);
-  const size_t o_hll = lay.add((size_t)kc::kHllRegs * 4);
-  const size_t o_fh = lay.add((size_t)nf_max * 4);
-  const size_t o_fo = lay.add((size_t)(nf_max + 1) * 8);
-  const size_t o_flo = lay.add((size_t)(nf_max + 1) * 4);
-  const size_t o_fc = lay.add((size_t)nf_max * 8);
-  const size_t o_look = lay.add((size_t)nf_max * 8);
-  const size_t o_kbuf = lay.add(s.cap * s.kw * 8);
-  const size_t o_sbuf = lay.add(s.cap * s.kw * 8);
-  const size_t o_meta = lay.add(sizeof(kc::Meta));
-  const size_t out_key_bytes = s.cap * s.kw * 8, out_cnt_bytes = s.cap * 4;
-  if (p->max_bytes && (uint64_t)(lay.total + out_key_bytes + out_cnt_bytes) > p->max_bytes)
+  Job j;
+  plan_job(p, reads, offsets, n_reads, L, off_dev, k, canonical, j);
+  if (p->max_bytes && (uint64_t)(j.ws_bytes + j.out_key_bytes + j.out_cnt_bytes) > p->max_bytes)
     return fail(KC_ENOMEM, "kc_count: input needs more device memory than max_device_bytes");
-  if (p->ws_bytes < lay.total) {
+  if (p->ws_bytes < j.ws_bytes) {
     dev_free(p, p->ws);
     p->ws = nullptr;
     p->ws_bytes = 0;
-    void* w = dev_alloc(p, lay.total);
+    void* w = dev_alloc(p, j.ws_bytes);
     if (!w) return fail(KC_ENOMEM, "kc_count: scratch allocation failed");
     p->ws = w;
-    p->ws_bytes = lay.total;
+    p->ws_bytes = j.ws_bytes;
   }
-  uint8_t* ws = (uint8_t*)p->ws;
-  void* okeys = dev_alloc(p, out_key_bytes);
-  void* ocnts = okeys ? dev_alloc(p, out_cnt_bytes) : nullptr;
-  if (!okeys || !ocnts) {
-    dev_free(p, okeys);
+  j.okeys = dev_alloc(p, j.out_key_bytes);
+  j.ocnts = j.okeys ? dev_alloc(p, j.out_cnt_bytes) : nullptr;
+  if (!j.okeys || !j.ocnts) {
+    dev_free(p, j.okeys);
     return fail(KC_ENOMEM, "kc_count: result allocation failed");
   }
-
-  kc::Buffers b{};
-  b.reads = copy_reads ? (const uint8_t*)(ws + o_reads) : reads;
-  b.offsets = off_dev ? offsets : (const uint64_t*)(ws + o_offs);
-  b.codes64 = (uint64_t*)(ws + o_codes);
-  b.inv32 = (uint32_t*)(ws + o_inv);
-  b.tile_first = (uint64_t*)(ws + o_tf);
-  b.hist = (uint32_t*)(ws + o_hist);
-  b.toff = (uint64_t*)(ws + o_toff);
-  b.cstart = (uint64_t*)(ws + o_cst);
-  b.fine_base = (uint32_t*)(ws + o_fb);
-  b.fine_m = (uint32_t*)(ws + o_fl);
-  b.hll = (uint32_t*)(ws + o_hll);
-  b.fhist = (uint32_t*)(ws + o_fh);
-  b.foff = (uint64_t*)(ws + o_fo);
-  b.flo = (uint32_t*)(ws + o_flo);
-  b.fcur = (unsigned long long*)(ws + o_fc);
-  b.look = (unsigned long long*)(ws + o_look);
-  b.kbuf = (uint64_t*)(ws + o_kbuf);
-  b.sbuf = (uint64_t*)(ws + o_sbuf);
-  b.meta = (kc::Meta*)(ws + o_meta);
-  b.out_keys = (uint64_t*)okeys;
-  b.out_counts = (uint32_t*)ocnts;
-
   // on any error: let the launched work finish before its buffers go back to the allocator
   auto bail = [&](kc_status stc, const std::string& msg) {
     cudaStreamSynchronize(st);
     cudaGetLastError();
-    dev_free(p, okeys);
-    dev_free(p, ocnts);
+    dev_free(p, j.okeys);
+    dev_free(p, j.ocnts);
     return fail(stc, msg);
   };
-  if (copy_reads &&
-      (e = cudaMemcpyAsync((void*)b.reads, reads, L, reads_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) !=
-          cudaSuccess)
-    return bail(KC_ECUDA, std::string("kc_count: copying reads: ") + cudaGetErrorString(e));
-  if (!off_dev &&
-      (e = cudaMemcpyAsync((void*)b.offsets, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return bail(KC_ECUDA, std::string("kc_count: copying offsets: ") + cudaGetErrorString(e));
-  if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.fhist, 0, (size_t)nf_max * 4, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.look, 0, (size_t)nf_max * 8, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.cstart, 0, (size_t)(P1 + 1) * 8, st)) != cudaSuccess)
-    return bail(KC_ECUDA, std::string("kc_count: clearing scratch: ") + cudaGetErrorString(e));
 
   kc::Marker mark;
   p->n_marks = 0;
@@ -409,17 +522,11 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
     mark.fn = debug_mark;
     mark.ctx = p;
   }
-  int launches = kc::launch_phase1(s, b, p->n_sms, (void*)st, mark);
-  if (launches >= 0) {
-    const int l2 = kc::launch_phase2(s, b, p->n_sms, nf_max, (void*)st, mark);
-    launches = l2 >= 0 ? launches + l2 : l2;
-  }
-  if (launches < 0)
-    return bail(KC_ECUDA, std::string("kc_count: launch: ") + cudaGetErrorString((cudaError_t)(-launches)));
   kc::Meta m{};
-  if ((e = cudaMemcpyAsync(&m, b.meta, sizeof(m), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return bail(KC_ECUDA, std::string("kc_count: ") + cudaGetErrorString(e));
+  int launches = 0;
+  std::string err;
+  if (!enqueue_job(j, (uint8_t*)p->ws, st, &m, mark, p->n_sms, &launches, &err)) return bail(KC_ECUDA, "kc_count: " + err);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(KC_ECUDA, std::string("kc_count: ") + cudaGetErrorString(e));
   p->stats.kernel_launches = (uint32_t)launches;
   if (p->profile) {
     for (int i = 0; i < p->n_marks; ++i) {
@@ -429,24 +536,130 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
     }
     p->n_kernel_ms = p->n_marks;
   }
-  p->stats.n_partitions = (uint32_t)P1;
-  p->stats.n_fine = m.n_fine;
-  p->stats.n_overflow_fine = m.n_overflow;
-  p->stats.n_deferred_fine = m.n_deferred;
-  for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
-  for (int i = 0; i < 8; ++i) p->stats.sub_cycles[i] = m.sub_cycles[i];
-  if (m.status & kc::ST_BAD_OFFSETS) return bail(KC_EINVAL, "kc_count: offsets must start at 0 and be non-decreasing");
-  if (m.status & kc::ST_PARTITION_OVERFLOW)
-    return bail(KC_EOVERFLOW, "kc_count: one key range holds 2^32 windows or more; use more partitions");
-  if (m.status & kc::ST_COUNT_OVERFLOW) return bail(KC_EOVERFLOW, "kc_count: a count exceeds 2^32 - 1");
-  if (m.status & kc::ST_TIMEOUT) return bail(KC_ETIMEOUT, "kc_count: a device-side wait timed out");
-  if (m.status & kc::ST_INTERNAL) return bail(KC_ECUDA, "kc_count: internal consistency check failed");
-  out->n = m.n_distinct;
-  out->key_words = (uint32_t)s.kw;
-  out->keys = okeys;
-  out->counts = (uint32_t*)ocnts;
-  out->n_valid_windows = m.n_windows;
-  out->capacity = s.cap;
+  record_stats(p, j, m);
+  std::string msg;
+  const kc_status stc = job_status(m, "kc_count", &msg);
+  if (stc != KC_OK) return bail(stc, msg);
+  fill_result(j, m, out);
+  return KC_OK;
+}
+
+kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* reads, const uint64_t* const* offsets,
+                         const uint64_t* n_reads, const uint64_t* n_bases, int k, int canonical, kc_result* out) {
+  g_err.clear();
+  if (!p || !out) return fail(KC_EINVAL, "kc_count_batch: plan and out must not be NULL");
+  for (uint32_t i = 0; i < n_samples; ++i) memset(&out[i], 0, sizeof(out[i]));
+  if (n_samples == 0) return KC_OK;
+  if (!reads || !offsets || !n_reads || !n_bases) return fail(KC_EINVAL, "kc_count_batch: NULL sample array");
+  if (k < 1 || k > 64) return fail(KC_EINVAL, "kc_count_batch: k must be in 1..64");
+  ScopedBusy busy(p);
+  if (!busy.ok) return fail(KC_EBUSY, "kc_count_batch: plan in use by another call");
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+
+  // ---- every sample's shape and scratch layout (host only; nothing is read back)
+  std::vector<Job> jobs(n_samples);
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    if (!offsets[i]) return fail(KC_EINVAL, "kc_count_batch: offsets of a sample is NULL");
+    const bool off_dev = is_device_ptr(offsets[i]);
+    if (!off_dev) {
+      if (offsets[i][0] != 0 || offsets[i][n_reads[i]] != n_bases[i])
+        return fail(KC_EINVAL, "kc_count_batch: a sample's offsets must run from 0 to its base count");
+      for (uint64_t r = 0; r < n_reads[i]; ++r)
+        if (offsets[i][r + 1] < offsets[i][r]) return fail(KC_EINVAL, "kc_count_batch: offsets must be non-decreasing");
+    }
+    if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_count_batch: reads of a sample is NULL");
+    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
+  }
+  // ---- lanes: the largest samples, in order, on the plan's stream and scratch; samples of at
+  // most kLaneSmallBases bases spread over extra streams with their own scratch (longest
+  // first onto the least loaded lane), so that several small samples share the GPU
+  std::vector<uint32_t> order(n_samples);
+  for (uint32_t i = 0; i < n_samples; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return jobs[a].L > jobs[b].L; });
+  std::vector<int> lane_of(n_samples, 0);
+  uint64_t load[kc_plan_s::kLanes + 1] = {};
+  size_t need[kc_plan_s::kLanes + 1] = {};
+  for (uint32_t i : order) {
+    int best = 0;
+    if (jobs[i].L <= kLaneSmallBases)
+      for (int l = 1; l <= kc_plan_s::kLanes; ++l)
+        if (load[l] < load[best]) best = l;
+    lane_of[i] = best;
+    load[best] += jobs[i].L + 1;
+    if (jobs[i].ws_bytes > need[best]) need[best] = jobs[i].ws_bytes;
+  }
+  size_t total = 0;
+  for (uint32_t i = 0; i < n_samples; ++i) total += jobs[i].out_key_bytes + jobs[i].out_cnt_bytes;
+  for (int l = 0; l <= kc_plan_s::kLanes; ++l) total += need[l];
+  if (p->max_bytes && total > p->max_bytes)
+    return fail(KC_ENOMEM, "kc_count_batch: the batch needs more device memory than max_device_bytes");
+  // scratch and streams (grown only, kept by the plan)
+  for (int l = 0; l <= kc_plan_s::kLanes; ++l) {
+    if (!need[l]) continue;
+    if (l > 0 && !p->lane_st[l - 1] && (e = cudaStreamCreateWithFlags(&p->lane_st[l - 1], cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "kc_count_batch: creating a stream");
+    cudaStream_t lst = l ? p->lane_st[l - 1] : p->stream;
+    void*& w = l ? p->lane_ws[l - 1] : p->ws;
+    size_t& wb = l ? p->lane_ws_bytes[l - 1] : p->ws_bytes;
+    if (wb < need[l]) {
+      dev_free_on(p, w, lst);
+      w = nullptr;
+      wb = 0;
+      w = dev_alloc_on(p, need[l], lst);
+      if (!w) return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
+      wb = need[l];
+    }
+  }
+  kc::Meta* metas = nullptr;
+  if ((e = cudaMallocHost((void**)&metas, sizeof(kc::Meta) * n_samples)) != cudaSuccess)
+    return cuda_fail(e, "kc_count_batch: pinned status buffer");
+  auto lane_stream = [&](int l) { return l ? p->lane_st[l - 1] : p->stream; };
+  auto sync_all = [&]() {
+    cudaError_t r = cudaSuccess;
+    for (int l = 0; l <= kc_plan_s::kLanes; ++l)
+      if (need[l]) {
+        const cudaError_t x = cudaStreamSynchronize(lane_stream(l));
+        if (r == cudaSuccess) r = x;
+      }
+    return r;
+  };
+  auto release = [&](kc_status stc, const std::string& msg) {
+    sync_all();
+    cudaGetLastError();
+    for (uint32_t i = 0; i < n_samples; ++i) {
+      dev_free_on(p, jobs[i].okeys, lane_stream(lane_of[i]));
+      dev_free_on(p, jobs[i].ocnts, lane_stream(lane_of[i]));
+      memset(&out[i], 0, sizeof(out[i]));
+    }
+    cudaFreeHost(metas);
+    return fail(stc, msg);
+  };
+  // ---- enqueue every sample; no host synchronisation until all are in flight
+  const kc::Marker none;
+  uint32_t launches = 0;
+  for (uint32_t i : order) {
+    Job& j = jobs[i];
+    const cudaStream_t lst = lane_stream(lane_of[i]);
+    j.okeys = dev_alloc_on(p, j.out_key_bytes, lst);
+    j.ocnts = j.okeys ? dev_alloc_on(p, j.out_cnt_bytes, lst) : nullptr;
+    if (!j.okeys || !j.ocnts) return release(KC_ENOMEM, "kc_count_batch: result allocation failed");
+    uint8_t* ws = (uint8_t*)(lane_of[i] ? p->lane_ws[lane_of[i] - 1] : p->ws);
+    int nl = 0;
+    std::string err;
+    if (!enqueue_job(j, ws, lst, &metas[i], none, p->n_sms, &nl, &err)) return release(KC_ECUDA, "kc_count_batch: " + err);
+    launches += (uint32_t)nl;
+  }
+  if ((e = sync_all()) != cudaSuccess) return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    std::string msg;
+    const kc_status stc = job_status(metas[i], "kc_count_batch", &msg);
+    if (stc != KC_OK) return release(stc, msg + " (sample " + std::to_string(i) + ")");
+  }
+  for (uint32_t i = 0; i < n_samples; ++i) fill_result(jobs[i], metas[i], &out[i]);
+  p->stats = kc_stats{};
+  p->stats.kernel_launches = launches;
+  cudaFreeHost(metas);
   return KC_OK;
 }
 

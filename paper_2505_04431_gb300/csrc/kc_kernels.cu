@@ -196,11 +196,12 @@ __device__ T block_exclusive_scan_pad(T* data, int n, T* warp_tmp) {
 }
 
 // ------------------------------------------------------------------ input checks
-__global__ void k_check_offsets(const uint64_t* offsets, uint64_t n_reads, Meta* meta) {
+__global__ void k_check_offsets(const uint64_t* offsets, uint64_t n_reads, uint64_t L, Meta* meta) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_reads; i += (uint64_t)gridDim.x * blockDim.x) {
     if (offsets[i + 1] < offsets[i]) atomicOr(&meta->status, ST_BAD_OFFSETS);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && offsets[0] != 0) atomicOr(&meta->status, ST_BAD_OFFSETS);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (offsets[0] != 0 || offsets[n_reads] != L))
+    atomicOr(&meta->status, ST_BAD_OFFSETS);
 }
 
 // first read whose start is >= the halo start of each tile (lower bound in offsets)
@@ -489,12 +490,20 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
   __shared__ uint64_t code_s[kPackThreads + 2];
   __shared__ uint32_t inv_s[kPackThreads + 2];
   __shared__ uint32_t st_s[kPackThreads + 2];
-  __shared__ uint64_t rcur_s;
+  __shared__ uint64_t rcur_s, len_s;
   const int t = threadIdx.x;
   const int P1 = 1 << s.b1;
   const uint64_t tile = blockIdx.x;
   for (int c = t; c < P1; c += kPackThreads) hist_s[c] = 0;
-  if (t == 0) rcur_s = b.tile_first[tile];
+  if (t == 0) {
+    rcur_s = b.tile_first[tile];
+    // bases read: never past the end the offsets give (a base count that disagrees with
+    // them is reported by k_check_offsets; the reads buffer is not overrun meanwhile)
+    const uint64_t e = b.offsets[s.n_reads];
+    len_s = e < s.L ? e : s.L;
+  }
+  __syncthreads();
+  const uint64_t len = len_s;
   for (int sub = 0; sub < kTileWords / kPackThreads; ++sub) {
     const uint64_t j0 = tile * kTileWords + (uint64_t)sub * kPackThreads;
     if (j0 >= s.n_words) break;
@@ -504,7 +513,7 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
         code_s[t] = code_s[kPackThreads + t];
         inv_s[t] = inv_s[kPackThreads + t];
       } else if (j0 + t >= 2) {
-        convert_word(b.reads, s.L, j0 + t - 2, code_s[t], inv_s[t]);
+        convert_word(b.reads, len, j0 + t - 2, code_s[t], inv_s[t]);
       } else {
         code_s[t] = 0;
         inv_s[t] = ~0u;
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
     uint64_t code = 0;
     uint32_t inv = ~0u;
     if (j < s.n_words) {
-      convert_word(b.reads, s.L, j, code, inv);
+      convert_word(b.reads, len, j, code, inv);
       b.codes64[j] = code;
       b.inv32[j] = inv;
     }
@@ -2039,7 +2048,7 @@ int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, con
   if (s.n_reads > 0) {
     const uint64_t want = (s.n_reads + 255) / 256, lim = (uint64_t)n_sms * 8;
     const unsigned g = (unsigned)(want < lim ? want : lim);
-    k_check_offsets<<<g, 256, 0, st>>>(b.offsets, s.n_reads, b.meta);
+    k_check_offsets<<<g, 256, 0, st>>>(b.offsets, s.n_reads, s.L, b.meta);
     ++launches;
     KC_STEP("k_check_offsets");
   }
