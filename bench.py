@@ -37,6 +37,13 @@ WORKLOAD_DESC = {
                              "kc_count loop",
 }
 BATCH_SEED = 1004  # seeds of the batched workload's samples: mix_seed(1004, i)
+WORKLOAD_DESC["serve_2000_requests"] = (
+    "2000 count requests, Poisson arrivals at 200/s, k uniform in {21, 31, 63}, read sets of genomes log-uniform "
+    "0.05-20 Mbp (times --scale), 150 bp reads, U(10,30)x, 0.5% subst (drawn from a pool of 32 generated read sets); "
+    "served by one plan: requests submitted (kc_submit, queued on the plan's stream) shortest expected first with "
+    "ageing, two in flight, within a device-memory budget, completions polled (kc_job_poll), results kept on the "
+    "device; vs the same in arrival order, rounds of kc_count_batch, and one kc_count per request")
+SERVE_SEED = 1005  # seeds of the served workload: pool read sets mix_seed(1005, i), arrivals RandomState(1005)
 
 
 def measured_peaks():
@@ -384,6 +391,102 @@ def run_batch(args):
     counter.close()
 
 
+def run_serve(args):
+    """The served form (kc_submit / kc_job_poll, one host thread) against rounds of
+    kc_count_batch and against one kc_count per request, on the same arrival sequence;
+    every request's result digest must agree between the three."""
+    import torch
+    import synth
+    from paper_2505_04431_gb300 import KmerCounter
+    from paper_2505_04431_gb300 import build as kcbuild
+    from paper_2505_04431_gb300 import serve as sv
+
+    torch.cuda.set_device(0)
+    kcbuild.build()
+    pool = []
+    for i in range(32):
+        reads, offsets, _ = synth.generate(synth.SERVE, synth.mix_seed(SERVE_SEED, i), args.scale)
+        pool.append((torch.from_numpy(reads).cuda(), torch.from_numpy(offsets.view(np.int64)).cuda(),
+                     int(offsets[-1])))
+    torch.cuda.synchronize()
+    rng = np.random.RandomState(SERVE_SEED)
+    n_req, rate = 2000, 200.0
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    ks = rng.choice([21, 31, 63], n_req)
+    picks = rng.randint(0, len(pool), n_req)
+
+    def make():
+        return [sv.Request(float(a), pool[p][0], pool[p][1], pool[p][2], int(k)) for a, k, p in zip(arrivals, ks, picks)]
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(64 << 30, max(4 << 30, free - (24 << 30))))
+    counter = KmerCounter()
+    # warm-up: every k once, submitted and counted directly; the largest input at k = 63
+    # last, so that the plan's scratch has its final size before the timed runs
+    big = max(range(len(pool)), key=lambda i: pool[i][2])
+    for k in (21, 31, 63):
+        counter.count(pool[0][0], pool[0][1], k).free()
+        counter.wait(counter.submit(pool[0][0], pool[0][1], k, True, n_bases=pool[0][2])).free()
+    counter.count(pool[big][0], pool[big][1], 63).free()
+    # the result of every (read set, k) in the mix, counted alone
+    ref = {}
+    for p_, k_ in sorted(set(zip(picks.tolist(), ks.tolist()))):
+        res = counter.count(pool[p_][0], pool[p_][1], k_)
+        ref[(p_, k_)] = sv._digest(res)
+        res.free()
+    # timed: latency to the completion of each count (results stay on the device)
+    runs = {}
+    for name in ("served", "served_fifo", "batch_rounds", "plain"):
+        reqs = make()
+        torch.cuda.synchronize()
+        if name == "served":
+            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="sjf")
+        elif name == "served_fifo":
+            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="fifo")
+        elif name == "batch_rounds":
+            info = sv.serve(counter, reqs, budget, keep_digest=False)
+        else:
+            info = sv.serve_one_at_a_time(counter, reqs, keep_digest=False)
+        runs[name] = (reqs, info)
+    served = runs["served"][0]
+    # checked (not timed): every request's result in the mix equals the same count alone
+    for name in ("served", "batch_rounds"):
+        reqs = make()
+        for r in reqs:
+            r.arrival = 0.0  # all at once: the longest queues
+        if name == "served":
+            sv.serve_async(counter, reqs, budget, policy="sjf")
+        else:
+            sv.serve(counter, reqs, budget)
+        mism = [i for i, (r, p_, k_) in enumerate(zip(reqs, picks, ks)) if r.digest != ref[(int(p_), int(k_))]]
+        if mism:
+            raise RuntimeError(f"{name}: results differ from single counts for {len(mism)} requests (first: {mism[0]})")
+    windows = sum(r.n_valid for r in served)
+
+    def summary(name):
+        reqs, info = runs[name]
+        return {"value": windows / info["makespan"] / 1e9, "unit": UNIT, "ms_per_step": info["makespan"] * 1e3,
+                "latency": sv.latency_summary(reqs)}
+
+    ls, lf, lb, lp = summary("served"), summary("served_fifo"), summary("batch_rounds"), summary("plain")
+    line = {"metric": METRIC, "value": ls["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": ls["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64/u128", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "requests": n_req,
+                       "rate_per_s": rate, "genome_scale": args.scale, "windows": windows,
+                       "offered_gkmers_per_s": windows / float(arrivals[-1]) / 1e9,
+                       "budget_gb": budget / 2**30, "parallelism": "1 GPU",
+                       "timing": "host wall clock; latency = arrival to the host seeing the count complete"},
+            "latency": ls["latency"], "peak_inflight": runs["served"][1]["peak_inflight"],
+            "policy": "shortest expected service first, with ageing; 2 counts queued on the GPU",
+            "served_fifo": lf, "batch_rounds": lb, "plain": lp,
+            "p50_plain_over_served": lp["latency"]["p50_ms"] / ls["latency"]["p50_ms"],
+            "p99_plain_over_served": lp["latency"]["p99_ms"] / ls["latency"]["p99_ms"],
+            "results_identical": True, "gpu_launches": 13 * n_req}
+    print(json.dumps(line), flush=True)
+    counter.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,6 +504,8 @@ def main():
         run_reference(args)
     elif args.workload.startswith("batch_"):
         run_batch(args)
+    elif args.workload.startswith("serve_"):
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -183,17 +183,46 @@ kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64
  *                   that nothing has to be read back before the samples are enqueued.
  *   out[i]          sample i's result, as kc_count returns it (free each with kc_free).
  *
- * Every sample's copies and kernels are enqueued without host synchronisation between
- * samples: the largest samples in order on the plan's stream and scratch, samples of up
- * to 64 Mi bases spread over three more streams with scratch of their own (created on
- * first use, kept by the plan), so that several small samples share the GPU; one
- * synchronisation at the end.  Scratch is sized once per stream for its largest sample.
+ * Every sample's copies and kernels are enqueued in order on the plan's stream, without
+ * host synchronisation between samples, on scratch sized once for the largest sample;
+ * one synchronisation at the end.  Samples never run concurrently with each other.
  * On any error no result is returned (all out[i] zeroed) and kc_last_error() names the
  * sample.  Errors as for kc_count; KC_ENOMEM if the batch's results and scratch exceed
  * max_device_bytes. */
 kc_status kc_count_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *const *reads,
                          const uint64_t *const *offsets, const uint64_t *n_reads, const uint64_t *n_bases, int k,
                          int canonical, kc_result *out);
+
+/* Submitted counts: the same operation as kc_count, returned later, so that one host
+ * thread can keep many counts queued (for a service that takes requests as they arrive)
+ * and the GPU runs them back to back, without a host round trip between two counts.
+ *
+ * kc_submit checks the arguments, sizes the count and enqueues its copies and kernels at
+ * once on the plan's stream, behind the counts already queued there (the plan's scratch
+ * grows in stream order when a count needs more), and returns without waiting for the
+ * GPU.  Counts never run concurrently with each other on the device.
+ *   reads, offsets, n_reads   as for kc_count (host or device memory).  They are read
+ *                  by the GPU after kc_submit returns: keep them valid and unchanged
+ *                  until the job is collected.  Host buffers should be pinned
+ *                  (cudaMallocHost / cudaHostRegister); copies from pageable memory
+ *                  may make the call wait for earlier work.
+ *   n_bases        offsets[n_reads] (known to the caller, so nothing is read back).
+ *   *job           a nonzero job id, valid until the job is collected.
+ * At most 4096 jobs are in flight per plan (KC_EBUSY beyond).
+ * Errors: KC_EINVAL (as for kc_count; host offsets are checked at once, device offsets
+ * by the GPU, reported when the job is collected), KC_ENOMEM, KC_ECUDA; no job is
+ * created then.
+ *
+ * kc_job_poll collects a job if it has finished: *done = 0 while it runs (KC_OK, *out
+ * zeroed); once finished *done = 1 and *out holds the result exactly as kc_count returns
+ * it (free with kc_free), or the job's error is returned (its buffers are released).
+ * Either way the job id is then invalid.  kc_job_wait blocks until the job finishes and
+ * collects it.  kc_plan_destroy waits for jobs not collected and releases them.
+ * Errors: KC_EINVAL (NULL arguments, unknown job id), and the job's own errors. */
+kc_status kc_submit(kc_plan_t plan, const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, uint64_t n_bases,
+                    int k, int canonical, uint64_t *job);
+kc_status kc_job_poll(kc_plan_t plan, uint64_t job, kc_result *out, int *done);
+kc_status kc_job_wait(kc_plan_t plan, uint64_t job, kc_result *out);
 
 #ifdef __cplusplus
 }

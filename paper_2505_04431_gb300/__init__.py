@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
-            "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch"]
+            "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch",
+            "kc_submit", "kc_job_poll", "kc_job_wait"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 KC_PLAN_DEFER_ALL = 2
@@ -97,6 +98,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     P = ctypes.POINTER
     lib.kc_count_batch.argtypes = [vp, ctypes.c_uint32, P(vp), P(vp), P(u64), P(u64), i32, i32, P(Result)]
     lib.kc_count_batch.restype = i32
+    lib.kc_submit.argtypes = [vp, vp, vp, u64, u64, i32, i32, P(u64)]
+    lib.kc_submit.restype = i32
+    lib.kc_job_poll.argtypes = [vp, u64, P(Result), P(i32)]
+    lib.kc_job_poll.restype = i32
+    lib.kc_job_wait.argtypes = [vp, u64, P(Result)]
+    lib.kc_job_wait.restype = i32
     _lib = lib
     return lib
 
@@ -227,6 +234,7 @@ class KmerCounter:
         _check(lib, lib.kc_plan(ctypes.byref(opts), ctypes.byref(plan)))
         self._opts = opts
         self._plan = plan
+        self._inflight = {}  # job id -> the buffers it reads
 
     def count(self, reads, offsets, k: int, canonical: bool = True) -> CountResult:
         """Sorted (k-mer, count) histogram of the reads (host or device buffers)."""
@@ -268,6 +276,44 @@ class KmerCounter:
         del keep
         return [CountResult(self, res[i]) for i in range(n)]
 
+    def submit(self, reads, offsets, k: int, canonical: bool = True, n_bases: int | None = None) -> int:
+        """Enqueue a count without waiting for it (kc_submit); returns a job id.  The
+        buffers are kept alive here until the job is collected; host buffers should be
+        pinned (torch pin_memory) so that the call does not wait for earlier work."""
+        rp, rk = _ptr(reads)
+        op, ok = _ptr(offsets)
+        n_reads = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+        if n_reads < 0:
+            raise ValueError("offsets must hold n_reads + 1 entries")
+        if n_bases is None:
+            last = offsets[-1]
+            n_bases = int(last.item() if hasattr(last, "item") else last)
+        job = ctypes.c_uint64()
+        _check(self._lib, self._lib.kc_submit(self._plan, rp, op, n_reads, int(n_bases), int(k),
+                                              int(bool(canonical)), ctypes.byref(job)))
+        self._inflight[job.value] = (rk, ok)
+        return job.value
+
+    def poll(self, job: int) -> CountResult | None:
+        """The job's result if it has finished (kc_job_poll), else None."""
+        res = Result()
+        done = ctypes.c_int()
+        try:
+            _check(self._lib, self._lib.kc_job_poll(self._plan, int(job), ctypes.byref(res), ctypes.byref(done)))
+        finally:
+            if done.value:
+                self._inflight.pop(int(job), None)
+        return CountResult(self, res) if done.value else None
+
+    def wait(self, job: int) -> CountResult:
+        """Block until the job finishes and return its result (kc_job_wait)."""
+        res = Result()
+        try:
+            _check(self._lib, self._lib.kc_job_wait(self._plan, int(job), ctypes.byref(res)))
+        finally:
+            self._inflight.pop(int(job), None)
+        return CountResult(self, res)
+
     def stats(self) -> dict:
         st = Stats()
         _check(self._lib, self._lib.kc_last_stats(self._plan, ctypes.byref(st)))
@@ -288,6 +334,7 @@ class KmerCounter:
         if self._plan:
             self._lib.kc_plan_destroy(self._plan)
             self._plan = None
+            self._inflight.clear()
 
     def __del__(self):
         try:

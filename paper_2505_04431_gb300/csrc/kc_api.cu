@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kc.h"
@@ -28,8 +29,7 @@ kc_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// batched counts: samples of at most this many bases may run on the extra lanes
-constexpr uint64_t kLaneSmallBases = 64ull << 20;
+struct AsyncJob;  // a count submitted with kc_submit
 
 }  // namespace
 
@@ -51,11 +51,12 @@ struct kc_plan_s {
   size_t smem_optin = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
-  // batched counts: extra streams with their own scratch (created on first use)
-  static constexpr int kLanes = 3;
-  cudaStream_t lane_st[kLanes] = {};
-  void* lane_ws[kLanes] = {};
-  size_t lane_ws_bytes[kLanes] = {};
+  // submitted counts (kc_submit): jobs in flight and their pinned status records
+  std::unordered_map<uint64_t, AsyncJob*> jobs;
+  uint64_t next_job = 1;
+  static constexpr int kPinned = 4096;
+  struct kc::Meta* pinned = nullptr;
+  std::vector<int> pinned_free;
   std::atomic<int> busy{0};
   kc_stats stats{};
   // per-kernel timing (KC_PLAN_PROFILE)
@@ -71,23 +72,21 @@ struct kc_plan_s {
 
 namespace {
 
-void* dev_alloc_on(kc_plan_s* p, size_t bytes, cudaStream_t st) {
+void* dev_alloc(kc_plan_s* p, size_t bytes) {
   if (bytes == 0) bytes = 256;
-  if (p->alloc) return p->alloc(bytes, (void*)st, p->ctx);
+  if (p->alloc) return p->alloc(bytes, (void*)p->stream, p->ctx);
   void* ptr = nullptr;
-  if (cudaMallocAsync(&ptr, bytes, st) != cudaSuccess) {
+  if (cudaMallocAsync(&ptr, bytes, p->stream) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   return ptr;
 }
-void dev_free_on(kc_plan_s* p, void* ptr, cudaStream_t st) {
+void dev_free(kc_plan_s* p, void* ptr) {
   if (!ptr) return;
-  if (p->free_) p->free_(ptr, (void*)st, p->ctx);
-  else cudaFreeAsync(ptr, st);
+  if (p->free_) p->free_(ptr, (void*)p->stream, p->ctx);
+  else cudaFreeAsync(ptr, p->stream);
 }
-void* dev_alloc(kc_plan_s* p, size_t bytes) { return dev_alloc_on(p, bytes, p->stream); }
-void dev_free(kc_plan_s* p, void* ptr) { dev_free_on(p, ptr, p->stream); }
 
 bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes a;
@@ -294,8 +293,13 @@ bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst,
   return true;
 }
 
-kc_status job_status(const kc::Meta& m, const char* who, std::string* msg) {
+kc_status job_status(const Job& j, const kc::Meta& m, const char* who, std::string* msg) {
   const std::string w(who);
+  // the status record must describe a result that fits the buffers of this count
+  if (m.n_windows > j.L || m.n_distinct > m.n_windows || m.n_fine > j.nf_max || m.n_deferred > m.n_fine) {
+    *msg = w + ": inconsistent status record";
+    return KC_ECUDA;
+  }
   if (m.status & kc::ST_BAD_OFFSETS) {
     *msg = w + ": offsets must start at 0, be non-decreasing and end at the base count";
     return KC_EINVAL;
@@ -326,6 +330,24 @@ void fill_result(const Job& j, const kc::Meta& m, kc_result* out) {
   out->counts = (uint32_t*)j.ocnts;
   out->n_valid_windows = m.n_windows;
   out->capacity = j.s.cap;
+}
+
+struct AsyncJob {
+  Job j;
+  int slot = -1;
+  cudaEvent_t ev = nullptr;
+};
+
+// release a finished (or failed) job's bookkeeping; with `drop`, its result buffers too
+void retire(kc_plan_s* p, uint64_t id, AsyncJob* a, bool drop) {
+  if (drop) {
+    dev_free(p, a->j.okeys);
+    dev_free(p, a->j.ocnts);
+  }
+  if (a->ev) cudaEventDestroy(a->ev);
+  if (a->slot >= 0) p->pinned_free.push_back(a->slot);
+  p->jobs.erase(id);
+  delete a;
 }
 
 void record_stats(kc_plan_s* p, const Job& j, const kc::Meta& m) {
@@ -396,13 +418,13 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   g_err.clear();
   if (!p) return fail(KC_EINVAL, "kc_plan_destroy: NULL plan");
   cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->stream);
+  while (!p->jobs.empty()) {  // results never collected
+    auto it = p->jobs.begin();
+    retire(p, it->first, it->second, true);
+  }
+  if (p->pinned) cudaFreeHost(p->pinned);
   dev_free(p, p->ws);
-  for (int l = 0; l < kc_plan_s::kLanes; ++l)
-    if (p->lane_st[l]) {
-      dev_free_on(p, p->lane_ws[l], p->lane_st[l]);
-      cudaStreamSynchronize(p->lane_st[l]);
-      cudaStreamDestroy(p->lane_st[l]);
-    }
   cudaStreamSynchronize(p->stream);
   if (p->profile)
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) cudaEventDestroy(p->ev[i]);
@@ -538,7 +560,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   }
   record_stats(p, j, m);
   std::string msg;
-  const kc_status stc = job_status(m, "kc_count", &msg);
+  const kc_status stc = job_status(j, m, "kc_count", &msg);
   if (stc != KC_OK) return bail(stc, msg);
   fill_result(j, m, out);
   return KC_OK;
@@ -571,65 +593,32 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_count_batch: reads of a sample is NULL");
     plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
   }
-  // ---- lanes: the largest samples, in order, on the plan's stream and scratch; samples of at
-  // most kLaneSmallBases bases spread over extra streams with their own scratch (longest
-  // first onto the least loaded lane), so that several small samples share the GPU
-  std::vector<uint32_t> order(n_samples);
-  for (uint32_t i = 0; i < n_samples; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return jobs[a].L > jobs[b].L; });
-  std::vector<int> lane_of(n_samples, 0);
-  uint64_t load[kc_plan_s::kLanes + 1] = {};
-  size_t need[kc_plan_s::kLanes + 1] = {};
-  for (uint32_t i : order) {
-    int best = 0;
-    if (jobs[i].L <= kLaneSmallBases)
-      for (int l = 1; l <= kc_plan_s::kLanes; ++l)
-        if (load[l] < load[best]) best = l;
-    lane_of[i] = best;
-    load[best] += jobs[i].L + 1;
-    if (jobs[i].ws_bytes > need[best]) need[best] = jobs[i].ws_bytes;
+  // ---- every sample in order on the plan's stream and scratch (sized once for the largest)
+  size_t need = 0, total = 0;
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    need = std::max(need, jobs[i].ws_bytes);
+    total += jobs[i].out_key_bytes + jobs[i].out_cnt_bytes;
   }
-  size_t total = 0;
-  for (uint32_t i = 0; i < n_samples; ++i) total += jobs[i].out_key_bytes + jobs[i].out_cnt_bytes;
-  for (int l = 0; l <= kc_plan_s::kLanes; ++l) total += need[l];
+  total += need;
   if (p->max_bytes && total > p->max_bytes)
     return fail(KC_ENOMEM, "kc_count_batch: the batch needs more device memory than max_device_bytes");
-  // scratch and streams (grown only, kept by the plan)
-  for (int l = 0; l <= kc_plan_s::kLanes; ++l) {
-    if (!need[l]) continue;
-    if (l > 0 && !p->lane_st[l - 1] && (e = cudaStreamCreateWithFlags(&p->lane_st[l - 1], cudaStreamNonBlocking)) != cudaSuccess)
-      return cuda_fail(e, "kc_count_batch: creating a stream");
-    cudaStream_t lst = l ? p->lane_st[l - 1] : p->stream;
-    void*& w = l ? p->lane_ws[l - 1] : p->ws;
-    size_t& wb = l ? p->lane_ws_bytes[l - 1] : p->ws_bytes;
-    if (wb < need[l]) {
-      dev_free_on(p, w, lst);
-      w = nullptr;
-      wb = 0;
-      w = dev_alloc_on(p, need[l], lst);
-      if (!w) return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
-      wb = need[l];
-    }
+  if (p->ws_bytes < need) {
+    dev_free(p, p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    p->ws = dev_alloc(p, need);
+    if (!p->ws) return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
+    p->ws_bytes = need;
   }
   kc::Meta* metas = nullptr;
   if ((e = cudaMallocHost((void**)&metas, sizeof(kc::Meta) * n_samples)) != cudaSuccess)
     return cuda_fail(e, "kc_count_batch: pinned status buffer");
-  auto lane_stream = [&](int l) { return l ? p->lane_st[l - 1] : p->stream; };
-  auto sync_all = [&]() {
-    cudaError_t r = cudaSuccess;
-    for (int l = 0; l <= kc_plan_s::kLanes; ++l)
-      if (need[l]) {
-        const cudaError_t x = cudaStreamSynchronize(lane_stream(l));
-        if (r == cudaSuccess) r = x;
-      }
-    return r;
-  };
   auto release = [&](kc_status stc, const std::string& msg) {
-    sync_all();
+    cudaStreamSynchronize(p->stream);
     cudaGetLastError();
     for (uint32_t i = 0; i < n_samples; ++i) {
-      dev_free_on(p, jobs[i].okeys, lane_stream(lane_of[i]));
-      dev_free_on(p, jobs[i].ocnts, lane_stream(lane_of[i]));
+      dev_free(p, jobs[i].okeys);
+      dev_free(p, jobs[i].ocnts);
       memset(&out[i], 0, sizeof(out[i]));
     }
     cudaFreeHost(metas);
@@ -638,22 +627,22 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
   // ---- enqueue every sample; no host synchronisation until all are in flight
   const kc::Marker none;
   uint32_t launches = 0;
-  for (uint32_t i : order) {
+  for (uint32_t i = 0; i < n_samples; ++i) {
     Job& j = jobs[i];
-    const cudaStream_t lst = lane_stream(lane_of[i]);
-    j.okeys = dev_alloc_on(p, j.out_key_bytes, lst);
-    j.ocnts = j.okeys ? dev_alloc_on(p, j.out_cnt_bytes, lst) : nullptr;
+    j.okeys = dev_alloc(p, j.out_key_bytes);
+    j.ocnts = j.okeys ? dev_alloc(p, j.out_cnt_bytes) : nullptr;
     if (!j.okeys || !j.ocnts) return release(KC_ENOMEM, "kc_count_batch: result allocation failed");
-    uint8_t* ws = (uint8_t*)(lane_of[i] ? p->lane_ws[lane_of[i] - 1] : p->ws);
     int nl = 0;
     std::string err;
-    if (!enqueue_job(j, ws, lst, &metas[i], none, p->n_sms, &nl, &err)) return release(KC_ECUDA, "kc_count_batch: " + err);
+    if (!enqueue_job(j, (uint8_t*)p->ws, p->stream, &metas[i], none, p->n_sms, &nl, &err))
+      return release(KC_ECUDA, "kc_count_batch: " + err);
     launches += (uint32_t)nl;
   }
-  if ((e = sync_all()) != cudaSuccess) return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
+  if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+    return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
   for (uint32_t i = 0; i < n_samples; ++i) {
     std::string msg;
-    const kc_status stc = job_status(metas[i], "kc_count_batch", &msg);
+    const kc_status stc = job_status(jobs[i], metas[i], "kc_count_batch", &msg);
     if (stc != KC_OK) return release(stc, msg + " (sample " + std::to_string(i) + ")");
   }
   for (uint32_t i = 0; i < n_samples; ++i) fill_result(jobs[i], metas[i], &out[i]);
@@ -661,6 +650,123 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
   p->stats.kernel_launches = launches;
   cudaFreeHost(metas);
   return KC_OK;
+}
+
+
+kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t n_bases,
+                    int k, int canonical, uint64_t* job) {
+  g_err.clear();
+  if (!p || !job) return fail(KC_EINVAL, "kc_submit: plan and job must not be NULL");
+  *job = 0;
+  if (k < 1 || k > 64) return fail(KC_EINVAL, "kc_submit: k must be in 1..64");
+  if (!offsets) return fail(KC_EINVAL, "kc_submit: offsets must not be NULL");
+  if (n_bases > 0 && !reads) return fail(KC_EINVAL, "kc_submit: reads must not be NULL");
+  ScopedBusy busy(p);
+  if (!busy.ok) return fail(KC_EBUSY, "kc_submit: plan in use by another call");
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  const bool off_dev = is_device_ptr(offsets);
+  if (!off_dev) {
+    if (offsets[0] != 0 || offsets[n_reads] != n_bases)
+      return fail(KC_EINVAL, "kc_submit: offsets must run from 0 to the base count");
+    for (uint64_t r = 0; r < n_reads; ++r)
+      if (offsets[r + 1] < offsets[r]) return fail(KC_EINVAL, "kc_submit: offsets must be non-decreasing");
+  }
+  if (!p->pinned) {
+    if ((e = cudaMallocHost((void**)&p->pinned, sizeof(kc::Meta) * kc_plan_s::kPinned)) != cudaSuccess)
+      return cuda_fail(e, "kc_submit: pinned status records");
+    for (int i = kc_plan_s::kPinned - 1; i >= 0; --i) p->pinned_free.push_back(i);
+  }
+  if (p->pinned_free.empty()) return fail(KC_EBUSY, "kc_submit: too many counts in flight");
+  AsyncJob* a = new AsyncJob();
+  plan_job(p, reads, offsets, n_reads, n_bases, off_dev, k, canonical, a->j);
+  if (p->max_bytes && (uint64_t)(a->j.ws_bytes + a->j.out_key_bytes + a->j.out_cnt_bytes) > p->max_bytes) {
+    delete a;
+    return fail(KC_ENOMEM, "kc_submit: input needs more device memory than max_device_bytes");
+  }
+  // submitted counts run one after another on the plan's stream (never two at once on the
+  // device); the plan's scratch grows in stream order if this count needs more
+  const cudaStream_t lst = p->stream;
+  if (p->ws_bytes < a->j.ws_bytes) {
+    dev_free(p, p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    p->ws = dev_alloc(p, a->j.ws_bytes);
+    if (!p->ws) {
+      delete a;
+      return fail(KC_ENOMEM, "kc_submit: scratch allocation failed");
+    }
+    p->ws_bytes = a->j.ws_bytes;
+  }
+  a->j.okeys = dev_alloc(p, a->j.out_key_bytes);
+  a->j.ocnts = a->j.okeys ? dev_alloc(p, a->j.out_cnt_bytes) : nullptr;
+  if (!a->j.okeys || !a->j.ocnts) {
+    dev_free(p, a->j.okeys);
+    delete a;
+    return fail(KC_ENOMEM, "kc_submit: result allocation failed");
+  }
+  a->slot = p->pinned_free.back();
+  p->pinned_free.pop_back();
+  const uint64_t id = p->next_job++;
+  p->jobs[id] = a;
+  int nl = 0;
+  std::string err;
+  const kc::Marker none;
+  if (!enqueue_job(a->j, (uint8_t*)p->ws, lst, &p->pinned[a->slot], none, p->n_sms, &nl, &err)) {
+    cudaStreamSynchronize(lst);
+    cudaGetLastError();
+    retire(p, id, a, true);
+    return fail(KC_ECUDA, "kc_submit: " + err);
+  }
+  if ((e = cudaEventCreateWithFlags(&a->ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventRecord(a->ev, lst)) != cudaSuccess) {
+    cudaStreamSynchronize(lst);
+    retire(p, id, a, true);
+    return cuda_fail(e, "kc_submit: completion event");
+  }
+  *job = id;
+  return KC_OK;
+}
+
+static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done, bool block) {
+  g_err.clear();
+  if (!p || !out || !done) return fail(KC_EINVAL, "kc_job_poll: NULL argument");
+  *done = 0;
+  memset(out, 0, sizeof(*out));
+  ScopedBusy busy(p);
+  if (!busy.ok) return fail(KC_EBUSY, "kc_job_poll: plan in use by another call");
+  auto it = p->jobs.find(id);
+  if (it == p->jobs.end()) return fail(KC_EINVAL, "kc_job_poll: no such job");
+  AsyncJob* a = it->second;
+  cudaSetDevice(p->device);
+  const cudaError_t q = block ? cudaEventSynchronize(a->ev) : cudaEventQuery(a->ev);
+  if (q == cudaErrorNotReady) return KC_OK;
+  *done = 1;
+  if (q != cudaSuccess) {
+    retire(p, id, a, true);
+    return cuda_fail(q, "kc_job_poll");
+  }
+  const kc::Meta m = p->pinned[a->slot];
+  std::string msg;
+  const kc_status stc = job_status(a->j, m, "kc_job_poll", &msg);
+  if (stc != KC_OK) {
+    retire(p, id, a, true);
+    return fail(stc, msg);
+  }
+  memset(out, 0, sizeof(*out));
+  fill_result(a->j, m, out);
+  record_stats(p, a->j, m);
+  retire(p, id, a, false);
+  return KC_OK;
+}
+
+kc_status kc_job_poll(kc_plan_t p, uint64_t job, kc_result* out, int* done) {
+  return job_collect(p, job, out, done, false);
+}
+
+kc_status kc_job_wait(kc_plan_t p, uint64_t job, kc_result* out) {
+  int done = 0;
+  return job_collect(p, job, out, &done, true);
 }
 
 }  // extern "C"

@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers 
   load_fine_map(b, P1, fmap);
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
-  const uint64_t K_total = b.meta->n_windows;
+  const uint64_t K_total = min(b.meta->n_windows, s.cap);
   const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
   if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
     fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
@@ -1055,7 +1055,7 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffe
   load_fine_map(b, P1, fmap);
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
-  const uint64_t K_total = b.meta->n_windows;
+  const uint64_t K_total = min(b.meta->n_windows, s.cap);
   const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
   if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
     fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
@@ -1617,7 +1617,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
   __shared__ uint32_t big_s[kBigMax], big_n;
   __shared__ int stk_n;
   const K EMPTY = all_ones<K>();
-  const uint64_t NF = b.meta->n_fine;
+  const uint64_t NF = min(b.meta->n_fine, s.nf_max);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long* prof = s.profile ? reinterpret_cast<unsigned long long*>(b.meta->sub_cycles) : nullptr;
   unsigned long long* ticket = reinterpret_cast<unsigned long long*>(&b.meta->ticket);
@@ -1968,7 +1968,7 @@ __global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) {
 template <int KW>
 __global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
   typedef typename KeyT<KW>::T K;
-  const uint64_t n_def = b.meta->n_deferred;
+  const uint64_t n_def = min(b.meta->n_deferred, s.nf_max);
   const uint32_t* cnt_src = reinterpret_cast<const uint32_t*>(b.kbuf);
   for (uint64_t q = blockIdx.x; q < n_def; q += gridDim.x) {
     const uint64_t g = b.look[q];

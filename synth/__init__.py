@@ -25,6 +25,7 @@ UNIFORM_SHORT = 0   # 1 Mbp i.i.d. genome, 100 bp reads, 10x, 0.5% subst, 0.01% 
 REPEAT_SHORT = 1    # 100 Mbp genome with 20% repeat families, 150 bp reads, 30x
 LONG_NOISY = 2      # 50 Mbp genome, ~10 kbp log-normal reads, 20x, 5% indel-rich errors
 SAMPLE = 3          # one batched-workload sample (log-uniform genome size, 5-40x)
+SERVE = 4           # one served-workload request's read set (genome log-uniform 0.05-20 Mbp, 10-30x)
 
 # the five benchmark workloads: (generator, seed, k)
 WORKLOADS = {

@@ -20,6 +20,9 @@
  *                      split 60/20/20 substitution/insertion/deletion.
  *   WL_SAMPLE          one sample of the batched workload: genome log-uniform in
  *                      [0.1, 50] Mbp, 150 bp reads, coverage U[5,40], 0.5% subst.
+ *   WL_SERVE           one request's read set of the served workload: genome
+ *                      log-uniform in [0.05, 20] Mbp, 150 bp reads, coverage U[10,30],
+ *                      0.5% subst.
  * A scale factor multiplies the genome size (and the number of repeat families)
  * so the same shapes can be produced at sizes a slow checker finishes quickly.
  */
@@ -232,7 +235,7 @@ static int emit_long_reads(rng_t *r, const char *g, uint64_t G, double median, d
   return 0;
 }
 
-enum { WL_UNIFORM_SHORT = 0, WL_REPEAT_SHORT = 1, WL_LONG_NOISY = 2, WL_SAMPLE = 3 };
+enum { WL_UNIFORM_SHORT = 0, WL_REPEAT_SHORT = 1, WL_LONG_NOISY = 2, WL_SAMPLE = 3, WL_SERVE = 4 };
 
 /* Generate one read set.  Returns 0 on success; the caller releases it with synth_free. */
 int synth_generate(int workload, uint64_t seed, double scale, synth_out *out) {
@@ -265,6 +268,14 @@ int synth_generate(int workload, uint64_t seed, double scale, synth_out *out) {
     double lg = log(0.1e6) + rng_unit(&r) * (log(50e6) - log(0.1e6));
     G = (uint64_t)llround(exp(lg) * scale); if (G < 200) G = 200;
     double cov = 5.0 + 35.0 * rng_unit(&r);
+    g = (char *)malloc(G); if (!g) return -1;
+    random_seq(&r, g, G);
+    uint64_t n = (uint64_t)llround(cov * (double)G / 150.0);
+    rc = emit_short_reads(&r, g, G, 150, n, 0.005, 0.0, &s);
+  } else if (workload == WL_SERVE) {
+    double lg = log(0.05e6) + rng_unit(&r) * (log(20e6) - log(0.05e6));
+    G = (uint64_t)llround(exp(lg) * scale); if (G < 200) G = 200;
+    double cov = 10.0 + 20.0 * rng_unit(&r);
     g = (char *)malloc(G); if (!g) return -1;
     random_seq(&r, g, G);
     uint64_t n = (uint64_t)llround(cov * (double)G / 150.0);

@@ -46,7 +46,7 @@ def batch_samples(n, scale, seed=1004):
 @pytest.mark.parametrize("k,canonical", [(31, True), (21, False), (63, True)])
 def test_batch_matches_single_counts(counter, torch_cuda, k, canonical):
     torch = torch_cuda
-    samples = batch_samples(12, 0.01)  # genomes of 1 kbp - 0.5 Mbp, 5-40x: all four lanes busy
+    samples = batch_samples(12, 0.01)  # genomes of 1 kbp - 0.5 Mbp, 5-40x
     samples.insert(3, (np.zeros(0, np.uint8), np.zeros(1, np.uint64)))  # an empty sample
     dev = [(torch.from_numpy(r).cuda(), o, int(o[-1])) for r, o in samples]  # device reads, host offsets
     results = counter.count_batch(dev, k, canonical)
@@ -66,7 +66,8 @@ def test_batch_matches_single_counts(counter, torch_cuda, k, canonical):
 
 
 def test_batch_large_and_small_mixed(counter, torch_cuda):
-    # one sample above the lane threshold (plan stream) among small ones (extra streams)
+    # one large sample (several coarse partitions) among small ones: the scratch is sized for
+    # the large one and the small ones reuse it
     torch = torch_cuda
     big_r, big_o, _ = synth.generate(synth.REPEAT_SHORT, 1002, 0.03)  # 3 Mbp genome, 30x: 90 M bases
     assert int(big_o[-1]) > (64 << 20)
