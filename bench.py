@@ -347,21 +347,36 @@ def run_batch(args):
     counter = KmerCounter()
     t_plain, t_batch, valid = [], [], 0
 
-    def plain():
+    from paper_2505_04431_gb300 import serve as sv
+
+    def plain(digests=None):
         v = 0
         for r, o, _ in samples:
             res = counter.count(r, o, 31, True)
             v += res.n_valid_windows
+            if digests is not None:
+                digests.append(sv._digest(res))
             res.free()
         return v
 
-    def batched():
+    def batched(digests=None):
         out = counter.count_batch(samples, 31, True)
         v = sum(res.n_valid_windows for res in out)
+        if digests is not None:
+            digests.extend(sv._digest(res) for res in out)
         for res in out:
             res.free()
         return v
 
+    # checked once (not timed): every sample's result (distinct keys, windows, sums of keys
+    # and counts) is the same from the batch as from kc_count alone
+    dp, db = [], []
+    plain(dp)
+    batched(db)
+    mism = [i for i, (a, b) in enumerate(zip(dp, db)) if a != b]
+    if mism:
+        raise RuntimeError(f"batched results differ from kc_count for {len(mism)} samples (first: {mism[0]})")
+    launches = counter.stats()["kernel_launches"]
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -386,7 +401,8 @@ def run_batch(args):
                        "genome_scale": scale, "bases": bases, "windows": valid, "k": 31, "canonical": True,
                        "parallelism": "1 GPU", "timing": "host wall clock around all calls, median of steps"},
             "plain": {"value": valid / tp / 1e9, "unit": UNIT, "ms_per_step": tp * 1e3},
-            "batched_vs_plain": tp / tb, "gpu_launches": 13 * len(samples)}
+            "batched_vs_plain": tp / tb, "results_identical": True, "gpu_launches": launches,
+            "plain_gpu_launches": 13 * len(samples)}
     print(json.dumps(line), flush=True)
     counter.close()
 

@@ -73,6 +73,9 @@ typedef struct {
  * compaction pass moves it (the path taken when a partition's output offset is not yet
  * known when it is ready to write). */
 #define KC_PLAN_DEFER_ALL 2u
+/* Testing: kc_count_batch's scratch arena (counts that share batched launches) is limited
+ * to 32 MiB, so that small batches form several groups and larger counts run alone. */
+#define KC_PLAN_BATCH_ARENA_SMALL 4u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */
@@ -183,9 +186,13 @@ kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64
  *                   that nothing has to be read back before the samples are enqueued.
  *   out[i]          sample i's result, as kc_count returns it (free each with kc_free).
  *
- * Every sample's copies and kernels are enqueued in order on the plan's stream, without
- * host synchronisation between samples, on scratch sized once for the largest sample;
- * one synchronisation at the end.  Samples never run concurrently with each other.
+ * Samples are grouped so that a group's scratch fits one arena (16 GiB; a quarter of
+ * max_device_bytes when that is set), and every kernel of the path is launched once per
+ * group, each thread block working for one sample of the group (a table maps blocks to
+ * samples), so that many small samples fill the GPU together; a sample larger than the
+ * arena is counted alone.  Everything is enqueued on the plan's stream with one host
+ * synchronisation at the end.  The results of one group share two device allocations,
+ * released when the last of their results is freed with kc_free.
  * On any error no result is returned (all out[i] zeroed) and kc_last_error() names the
  * sample.  Errors as for kc_count; KC_ENOMEM if the batch's results and scratch exceed
  * max_device_bytes. */

@@ -31,6 +31,17 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct AsyncJob;  // a count submitted with kc_submit
 
+// The result buffers of a group of batched counts, shared by the group's results and
+// released with the last of them.
+struct GroupOwner {
+  void* keys = nullptr;
+  void* counts = nullptr;
+  std::atomic<int> refs{0};
+};
+
+// Scratch arena of one group of batched counts (their scratch side by side)
+constexpr size_t kBatchArenaBytes = 16ull << 30;
+
 }  // namespace
 
 namespace kc {
@@ -51,6 +62,13 @@ struct kc_plan_s {
   size_t smem_optin = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // batched counts: scratch arena of a group of counts, device and pinned host tables
+  void* bws = nullptr;
+  size_t bws_bytes = 0;
+  void* btab = nullptr;
+  size_t btab_bytes = 0;
+  void* btab_host = nullptr;
+  size_t btab_host_bytes = 0;
   // submitted counts (kc_submit): jobs in flight and their pinned status records
   std::unordered_map<uint64_t, AsyncJob*> jobs;
   uint64_t next_job = 1;
@@ -62,6 +80,7 @@ struct kc_plan_s {
   // per-kernel timing (KC_PLAN_PROFILE)
   bool profile = false;
   bool defer_all = false;
+  bool small_arena = false;
   static constexpr int kMaxMarks = 32;
   cudaEvent_t ev[kMaxMarks + 1] = {};
   const char* ev_name[kMaxMarks] = {};
@@ -230,11 +249,8 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   j.out_cnt_bytes = s.cap * 4;
 }
 
-// Copies, clears and launches of one count on stream `st` with scratch at `ws`; the
-// status record is copied to *meta_dst at the end (asynchronously if it is pinned).
-bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst, const kc::Marker& mark, int n_sms,
-                 int* launches, std::string* err) {
-  const kc::Shape& s = j.s;
+// The buffers of one count with scratch at `ws` and its outputs at j.okeys / j.ocnts.
+kc::Buffers make_buffers(const Job& j, uint8_t* ws) {
   kc::Buffers b{};
   b.reads = j.copy_reads ? (const uint8_t*)(ws + j.o_reads) : j.reads;
   b.offsets = j.off_dev ? j.offsets : (const uint64_t*)(ws + j.o_offs);
@@ -257,6 +273,11 @@ bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst,
   b.meta = (kc::Meta*)(ws + j.o_meta);
   b.out_keys = (uint64_t*)j.okeys;
   b.out_counts = (uint32_t*)j.ocnts;
+  return b;
+}
+
+// The input copies of one count (reads that are on the host or misaligned, host offsets).
+bool enqueue_copies(const Job& j, const kc::Buffers& b, cudaStream_t st, std::string* err) {
   cudaError_t e;
   if (j.copy_reads && (e = cudaMemcpyAsync((void*)b.reads, j.reads, j.L,
                                            j.reads_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) != cudaSuccess) {
@@ -268,6 +289,17 @@ bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst,
     *err = std::string("copying offsets: ") + cudaGetErrorString(e);
     return false;
   }
+  return true;
+}
+
+// Copies, clears and launches of one count on stream `st` with scratch at `ws`; the
+// status record is copied to *meta_dst at the end (asynchronously if it is pinned).
+bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst, const kc::Marker& mark, int n_sms,
+                 int* launches, std::string* err) {
+  const kc::Shape& s = j.s;
+  const kc::Buffers b = make_buffers(j, ws);
+  if (!enqueue_copies(j, b, st, err)) return false;
+  cudaError_t e;
   if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.fhist, 0, (size_t)j.nf_max * 4, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, st)) != cudaSuccess ||
@@ -401,6 +433,7 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->smem_optin = prop.sharedMemPerBlockOptin;
   p->profile = (opts->flags & KC_PLAN_PROFILE) != 0;
   p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
+  p->small_arena = (opts->flags & KC_PLAN_BATCH_ARENA_SMALL) != 0;
   if (p->profile) {
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) {
       if ((e = cudaEventCreate(&p->ev[i])) != cudaSuccess) {
@@ -424,6 +457,9 @@ kc_status kc_plan_destroy(kc_plan_t p) {
     retire(p, it->first, it->second, true);
   }
   if (p->pinned) cudaFreeHost(p->pinned);
+  if (p->btab_host) cudaFreeHost(p->btab_host);
+  dev_free(p, p->bws);
+  dev_free(p, p->btab);
   dev_free(p, p->ws);
   cudaStreamSynchronize(p->stream);
   if (p->profile)
@@ -436,8 +472,17 @@ kc_status kc_free(kc_plan_t p, kc_result* r) {
   g_err.clear();
   if (!p || !r) return fail(KC_EINVAL, "kc_free: NULL argument");
   cudaSetDevice(p->device);
-  dev_free(p, r->keys);
-  dev_free(p, r->counts);
+  if (r->_owner) {  // a result of a batched group: the group's buffers go with its last result
+    GroupOwner* o = (GroupOwner*)r->_owner;
+    if (o->refs.fetch_sub(1) == 1) {
+      dev_free(p, o->keys);
+      dev_free(p, o->counts);
+      delete o;
+    }
+  } else {
+    dev_free(p, r->keys);
+    dev_free(p, r->counts);
+  }
   memset(r, 0, sizeof(*r));
   return KC_OK;
 }
@@ -593,50 +638,173 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_count_batch: reads of a sample is NULL");
     plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
   }
-  // ---- every sample in order on the plan's stream and scratch (sized once for the largest)
-  size_t need = 0, total = 0;
+  // ---- groups: counts whose scratch fits the arena together share the batched launches
+  // (every kernel once per group); a count larger than the arena runs alone
+  const size_t arena_cap = p->small_arena ? (32ull << 20)
+                           : p->max_bytes   ? std::max<size_t>(p->max_bytes / 4, 1ull << 28)
+                                            : kBatchArenaBytes;
+  struct Group {
+    std::vector<uint32_t> idx;
+    std::vector<size_t> ws_off, key_off, cnt_off;
+    size_t ws = 0, keys = 0, cnts = 0, tab = 0;
+    uint64_t bases = 0;
+    uint32_t grid[kc::BK_N] = {};
+  };
+  std::vector<Group> groups;
+  std::vector<uint32_t> alone;
+  size_t need_single = 0, arena = 0, total = 0, tab_total = 0;
   for (uint32_t i = 0; i < n_samples; ++i) {
-    need = std::max(need, jobs[i].ws_bytes);
-    total += jobs[i].out_key_bytes + jobs[i].out_cnt_bytes;
+    const Job& j = jobs[i];
+    total += j.out_key_bytes + j.out_cnt_bytes;
+    const size_t w = align_up(j.ws_bytes, 256);
+    if (w > arena_cap) {
+      alone.push_back(i);
+      need_single = std::max(need_single, j.ws_bytes);
+      continue;
+    }
+    if (groups.empty() || groups.back().ws + w > arena_cap) groups.emplace_back();
+    Group& g = groups.back();
+    g.idx.push_back(i);
+    g.ws_off.push_back(g.ws);
+    g.key_off.push_back(g.keys);
+    g.cnt_off.push_back(g.cnts);
+    g.ws += w;
+    g.keys += align_up(j.out_key_bytes, 256);
+    g.cnts += align_up(j.out_cnt_bytes, 256);
+    g.bases += j.L;
   }
-  total += need;
+  for (Group& g : groups) {
+    arena = std::max(arena, g.ws);
+    const uint32_t n = (uint32_t)g.idx.size();
+    size_t words = 0;
+    for (int k = 0; k < kc::BK_N; ++k) {
+      uint64_t sum = 0;
+      for (uint32_t q : g.idx) sum += kc::batch_blocks((kc::BatchKernel)k, jobs[q].s, p->n_sms, g.bases);
+      if (sum > 0x7fffffffull) return fail(KC_EINVAL, "kc_count_batch: a group needs too many thread blocks");
+      g.grid[k] = (uint32_t)sum;
+      words += (n + 1) + sum;
+    }
+    g.tab = align_up(n * sizeof(kc::BatchDesc), 256) + align_up(words * 4, 256);
+    tab_total += g.tab;
+  }
+  total += arena + need_single + tab_total;
   if (p->max_bytes && total > p->max_bytes)
     return fail(KC_ENOMEM, "kc_count_batch: the batch needs more device memory than max_device_bytes");
-  if (p->ws_bytes < need) {
-    dev_free(p, p->ws);
-    p->ws = nullptr;
-    p->ws_bytes = 0;
-    p->ws = dev_alloc(p, need);
-    if (!p->ws) return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
-    p->ws_bytes = need;
+  auto grow = [&](void*& buf, size_t& have, size_t want) {
+    if (have >= want) return true;
+    dev_free(p, buf);
+    buf = nullptr;
+    have = 0;
+    buf = dev_alloc(p, want);
+    if (!buf) return false;
+    have = want;
+    return true;
+  };
+  if (!alone.empty() && !grow(p->ws, p->ws_bytes, need_single))
+    return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
+  if (!groups.empty() && (!grow(p->bws, p->bws_bytes, arena) || !grow(p->btab, p->btab_bytes, tab_total)))
+    return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
+  if (p->btab_host_bytes < tab_total) {
+    if (p->btab_host) cudaFreeHost(p->btab_host);
+    p->btab_host = nullptr;
+    p->btab_host_bytes = 0;
+    if ((e = cudaMallocHost(&p->btab_host, tab_total)) != cudaSuccess) return cuda_fail(e, "kc_count_batch: pinned tables");
+    p->btab_host_bytes = tab_total;
   }
   kc::Meta* metas = nullptr;
   if ((e = cudaMallocHost((void**)&metas, sizeof(kc::Meta) * n_samples)) != cudaSuccess)
     return cuda_fail(e, "kc_count_batch: pinned status buffer");
+  std::vector<GroupOwner*> owners(groups.size(), nullptr);
   auto release = [&](kc_status stc, const std::string& msg) {
     cudaStreamSynchronize(p->stream);
     cudaGetLastError();
-    for (uint32_t i = 0; i < n_samples; ++i) {
+    for (uint32_t i : alone) {
       dev_free(p, jobs[i].okeys);
       dev_free(p, jobs[i].ocnts);
-      memset(&out[i], 0, sizeof(out[i]));
     }
+    for (GroupOwner* o : owners)
+      if (o) {
+        dev_free(p, o->keys);
+        dev_free(p, o->counts);
+        delete o;
+      }
+    for (uint32_t i = 0; i < n_samples; ++i) memset(&out[i], 0, sizeof(out[i]));
     cudaFreeHost(metas);
     return fail(stc, msg);
   };
-  // ---- enqueue every sample; no host synchronisation until all are in flight
+  // ---- enqueue everything on the plan's stream; no host synchronisation until the end
   const kc::Marker none;
   uint32_t launches = 0;
-  for (uint32_t i = 0; i < n_samples; ++i) {
+  std::string err;
+  for (uint32_t i : alone) {
     Job& j = jobs[i];
     j.okeys = dev_alloc(p, j.out_key_bytes);
     j.ocnts = j.okeys ? dev_alloc(p, j.out_cnt_bytes) : nullptr;
     if (!j.okeys || !j.ocnts) return release(KC_ENOMEM, "kc_count_batch: result allocation failed");
     int nl = 0;
-    std::string err;
     if (!enqueue_job(j, (uint8_t*)p->ws, p->stream, &metas[i], none, p->n_sms, &nl, &err))
       return release(KC_ECUDA, "kc_count_batch: " + err);
     launches += (uint32_t)nl;
+  }
+  size_t tab_at = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    Group& g = groups[gi];
+    const uint32_t n = (uint32_t)g.idx.size();
+    GroupOwner* o = new GroupOwner();
+    owners[gi] = o;
+    o->keys = dev_alloc(p, g.keys);
+    o->counts = o->keys ? dev_alloc(p, g.cnts) : nullptr;
+    if (!o->keys || !o->counts) return release(KC_ENOMEM, "kc_count_batch: result allocation failed");
+    o->refs = (int)n;
+    // descriptors and block tables, staged in pinned memory and copied in one piece
+    uint8_t* h = (uint8_t*)p->btab_host + tab_at;
+    uint8_t* dv = (uint8_t*)p->btab + tab_at;
+    kc::BatchDesc* hd = (kc::BatchDesc*)h;
+    int P1_max = 1;
+    for (uint32_t q = 0; q < n; ++q) {
+      Job& j = jobs[g.idx[q]];
+      j.okeys = (uint8_t*)o->keys + g.key_off[q];
+      j.ocnts = (uint8_t*)o->counts + g.cnt_off[q];
+      hd[q].s = j.s;
+      hd[q].b = make_buffers(j, (uint8_t*)p->bws + g.ws_off[q]);
+      P1_max = std::max(P1_max, j.P1);
+      if (!enqueue_copies(j, hd[q].b, p->stream, &err)) return release(KC_ECUDA, "kc_count_batch: " + err);
+    }
+    kc::BatchPlan bp;
+    bp.n = (int)n;
+    bp.kw = jobs[g.idx[0]].s.kw;
+    bp.P1_max = P1_max;
+    bp.host = hd;
+    bp.desc = (const kc::BatchDesc*)dv;
+    uint32_t* hw = (uint32_t*)(h + align_up(n * sizeof(kc::BatchDesc), 256));
+    const uint32_t* dw = (const uint32_t*)(dv + align_up(n * sizeof(kc::BatchDesc), 256));
+    for (int k = 0; k < kc::BK_N; ++k) {
+      uint32_t* start = hw;
+      uint32_t* blk2s = hw + n + 1;
+      uint32_t at = 0;
+      for (uint32_t q = 0; q < n; ++q) {
+        start[q] = at;
+        const uint32_t c = kc::batch_blocks((kc::BatchKernel)k, jobs[g.idx[q]].s, p->n_sms, g.bases);
+        for (uint32_t x = 0; x < c; ++x) blk2s[at + x] = q;
+        at += c;
+      }
+      start[n] = at;
+      bp.start[k] = dw;
+      bp.blk2s[k] = dw + n + 1;
+      bp.grid[k] = at;
+      hw += n + 1 + at;
+      dw += n + 1 + at;
+    }
+    if ((e = cudaMemcpyAsync(dv, h, g.tab, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+      return release(KC_ECUDA, std::string("kc_count_batch: copying tables: ") + cudaGetErrorString(e));
+    const int nl = kc::launch_batch(bp, p->n_sms, (void*)p->stream, none);
+    if (nl < 0) return release(KC_ECUDA, std::string("kc_count_batch: launch: ") + cudaGetErrorString((cudaError_t)(-nl)));
+    launches += (uint32_t)nl;
+    for (uint32_t q = 0; q < n; ++q)
+      if ((e = cudaMemcpyAsync(&metas[g.idx[q]], hd[q].b.meta, sizeof(kc::Meta), cudaMemcpyDeviceToHost, p->stream)) !=
+          cudaSuccess)
+        return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
+    tab_at += g.tab;
   }
   if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
     return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
@@ -646,6 +814,8 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     if (stc != KC_OK) return release(stc, msg + " (sample " + std::to_string(i) + ")");
   }
   for (uint32_t i = 0; i < n_samples; ++i) fill_result(jobs[i], metas[i], &out[i]);
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    for (uint32_t q : groups[gi].idx) out[q]._owner = owners[gi];
   p->stats = kc_stats{};
   p->stats.kernel_launches = launches;
   cudaFreeHost(metas);

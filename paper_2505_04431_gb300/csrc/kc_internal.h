@@ -100,6 +100,38 @@ struct Buffers {
   Meta* meta;
 };
 
+// One count of a batch: its shape and its buffers (inside the batch's scratch arena).
+struct BatchDesc {
+  Shape s;
+  Buffers b;
+};
+
+// A batched launch of one kernel: block x works for count blk2s[x] as its block
+// x - start[blk2s[x]] of start[i + 1] - start[i].
+struct BatchTab {
+  const BatchDesc* desc;
+  const uint32_t* blk2s;
+  const uint32_t* start;
+};
+
+// The counts of a batch, laid out for the batched launches (host side; the device copy of
+// descriptors and tables is at `dev`).
+struct BatchPlan {
+  int n = 0;
+  int kw = 1;
+  int P1_max = 1;
+  const BatchDesc* host = nullptr;  // n descriptors
+  const BatchDesc* desc = nullptr;  // device copy
+  // per kernel: device block->count table and block starts (n + 1), and the grid
+  const uint32_t* blk2s[16] = {};
+  const uint32_t* start[16] = {};
+  uint32_t grid[16] = {};
+};
+enum BatchKernel {
+  BK_CLEAR, BK_CHECK, BK_TILE_FIRST, BK_PACK, BK_COL_SCAN, BK_BUCKET_SCAN, BK_SCATTER, BK_FINE_PLAN, BK_FINE_HIST,
+  BK_FINE_SCAN, BK_FINE_SCATTER, BK_COUNT, BK_SCAN_DISTINCT, BK_COMPACT, BK_N
+};
+
 // Called after every kernel launch with the kernel's name (used for per-kernel timing).
 struct Marker {
   void (*fn)(void* ctx, const char* name) = nullptr;
@@ -113,6 +145,11 @@ struct Marker {
 // -cudaError_t if a launch failed (no later kernel is launched then).
 int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, const Marker& mark);
 int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, void* stream, const Marker& mark);
+// Blocks each kernel of a batched launch gives one count (host rule, shared by the planner
+// and the launcher), and the whole batched launch sequence (returns launches or
+// -cudaError_t).
+uint32_t batch_blocks(BatchKernel k, const Shape& s, int n_sms, uint64_t bases_total);
+int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mark);
 int configure_kernels(int device);  // sets shared-memory attributes; returns 0 or a cudaError_t
 
 size_t count_kernel_smem(int kw, int bT_max, int tail);

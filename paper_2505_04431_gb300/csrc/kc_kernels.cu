@@ -40,6 +40,33 @@ namespace kc {
 
 typedef unsigned __int128 u128;
 
+// Batched launches: each block finds its count (one table load), copies the count's
+// descriptor to shared memory and runs the kernel body for that count.
+__device__ __forceinline__ void batch_locate(const BatchTab& t, BatchDesc& d_s, uint32_t& bid_s, uint32_t& nblk_s) {
+  __shared__ uint32_t i_s;
+  const uint32_t tid = threadIdx.x + threadIdx.y * blockDim.x, nth = blockDim.x * blockDim.y;
+  if (tid == 0) {
+    const uint32_t i = t.blk2s[blockIdx.x];
+    const uint32_t a = t.start[i];
+    i_s = i;
+    bid_s = blockIdx.x - a;
+    nblk_s = t.start[i + 1] - a;
+  }
+  __syncthreads();
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(t.desc + i_s);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&d_s);
+  for (uint32_t w = tid; w < sizeof(BatchDesc) / 4; w += nth) dst[w] = src[w];
+  __syncthreads();
+}
+#define KC_BATCH_PROLOGUE(t)                 \
+  __shared__ BatchDesc d_s_;                 \
+  __shared__ uint32_t bid_s_, nblk_s_;       \
+  batch_locate(t, d_s_, bid_s_, nblk_s_);    \
+  const BatchDesc& d = d_s_;                 \
+  const uint32_t bid = bid_s_, nblk = nblk_s_; \
+  (void)bid;                                 \
+  (void)nblk
+
 template <int KW> struct KeyT;
 template <> struct KeyT<1> { typedef uint64_t T; };
 template <> struct KeyT<2> { typedef u128 T; };
@@ -196,17 +223,42 @@ __device__ T block_exclusive_scan_pad(T* data, int n, T* warp_tmp) {
 }
 
 // ------------------------------------------------------------------ input checks
-__global__ void k_check_offsets(const uint64_t* offsets, uint64_t n_reads, uint64_t L, Meta* meta) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_reads; i += (uint64_t)gridDim.x * blockDim.x) {
+// Batched launches: the arrays a count needs zeroed (status record, fine histogram,
+// look-back words, sketch, partition starts) are cleared by one kernel for all counts.
+__global__ void k_clear_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  const Shape& s = d.s;
+  const Buffers& b = d.b;
+  const uint64_t i0 = (uint64_t)bid * blockDim.x + threadIdx.x, stride = (uint64_t)nblk * blockDim.x;
+  for (uint64_t i = i0; i < s.nf_max; i += stride) {
+    b.fhist[i] = 0;
+    b.look[i] = 0;
+  }
+  for (uint64_t i = i0; i < (uint64_t)kHllRegs; i += stride) b.hll[i] = 0;
+  for (uint64_t i = i0; i <= (1ull << s.b1); i += stride) b.cstart[i] = 0;
+  for (uint64_t i = i0; i < sizeof(Meta) / 4; i += stride) reinterpret_cast<uint32_t*>(b.meta)[i] = 0;
+}
+
+__device__ __forceinline__ void check_offsets_body(const uint64_t* offsets, uint64_t n_reads, uint64_t L, Meta* meta,
+                                                   uint32_t bid, uint32_t nblk) {
+  for (uint64_t i = bid * (uint64_t)blockDim.x + threadIdx.x; i < n_reads; i += (uint64_t)nblk * blockDim.x) {
     if (offsets[i + 1] < offsets[i]) atomicOr(&meta->status, ST_BAD_OFFSETS);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (offsets[0] != 0 || offsets[n_reads] != L))
+  if (bid == 0 && threadIdx.x == 0 && (offsets[0] != 0 || offsets[n_reads] != L))
     atomicOr(&meta->status, ST_BAD_OFFSETS);
+}
+__global__ void k_check_offsets(const uint64_t* offsets, uint64_t n_reads, uint64_t L, Meta* meta) {
+  check_offsets_body(offsets, n_reads, L, meta, blockIdx.x, gridDim.x);
+}
+__global__ void k_check_offsets_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  check_offsets_body(d.b.offsets, d.s.n_reads, d.s.L, d.b.meta, bid, nblk);
 }
 
 // first read whose start is >= the halo start of each tile (lower bound in offsets)
-__global__ void k_tile_first(const uint64_t* offsets, uint64_t n_reads, uint64_t n_tiles, uint64_t* tile_first) {
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void tile_first_body(const uint64_t* offsets, uint64_t n_reads, uint64_t n_tiles,
+                                                uint64_t* tile_first, uint32_t bid) {
+  const uint64_t t = bid * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
   const uint64_t pos = t * kTileBases;
   const uint64_t halo = pos >= 64 ? pos - 64 : 0;
@@ -216,6 +268,13 @@ __global__ void k_tile_first(const uint64_t* offsets, uint64_t n_reads, uint64_t
     if (offsets[mid] < halo) lo = mid + 1; else hi = mid;
   }
   tile_first[t] = lo;
+}
+__global__ void k_tile_first(const uint64_t* offsets, uint64_t n_reads, uint64_t n_tiles, uint64_t* tile_first) {
+  tile_first_body(offsets, n_reads, n_tiles, tile_first, blockIdx.x);
+}
+__global__ void k_tile_first_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  tile_first_body(d.b.offsets, d.s.n_reads, d.s.n_tiles, d.b.tile_first, bid);
 }
 
 // ------------------------------------------------------------------ phase 1 helpers
@@ -484,7 +543,7 @@ __device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t c1, int k, u128
 // One code word per thread: convert, store, and histogram the coarse partitions of its 32
 // windows (keys are recomputed in pass B, which needs the partition offsets first).
 template <int KW>
-__global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Shape s, Buffers b) {
+__device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b, uint32_t bid) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ uint32_t hist_s[];  // [P1]
   __shared__ uint64_t code_s[kPackThreads + 2];
@@ -493,7 +552,7 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
   __shared__ uint64_t rcur_s, len_s;
   const int t = threadIdx.x;
   const int P1 = 1 << s.b1;
-  const uint64_t tile = blockIdx.x;
+  const uint64_t tile = bid;
   for (int c = t; c < P1; c += kPackThreads) hist_s[c] = 0;
   if (t == 0) {
     rcur_s = b.tile_first[tile];
@@ -549,13 +608,23 @@ __global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Sh
   __syncthreads();
   for (int c = t; c < P1; c += kPackThreads) b.hist[tile * P1 + c] = hist_s[c];
 }
+template <int KW>
+__global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count(Shape s, Buffers b) {
+  pack_count_body<KW>(s, b, blockIdx.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(kPackThreads, KW == 1 ? 2 : 1) k_pack_count_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  pack_count_body<KW>(d.s, d.b, bid);
+}
 
 // ------------------------------------------------------------------ scans
 // Column scan of hist[tile][c]: toff[tile][c] = keys of partition c in tiles before `tile`.
-__global__ void k_col_scan(const uint32_t* hist, uint64_t* toff, uint64_t* ccount, uint64_t n_tiles, int P1) {
+__device__ __forceinline__ void col_scan_body(const uint32_t* hist, uint64_t* toff, uint64_t* ccount, uint64_t n_tiles, int P1,
+                                              uint32_t bid) {
   __shared__ uint64_t part[32][33];
   const int lane = threadIdx.x, w = threadIdx.y;
-  const int c = blockIdx.x * 32 + lane;
+  const int c = bid * 32 + lane;
   const uint64_t per = (n_tiles + 31) / 32;
   const uint64_t lo = min(n_tiles, (uint64_t)w * per), hi = min(n_tiles, lo + per);
   uint64_t s = 0;
@@ -581,9 +650,16 @@ __global__ void k_col_scan(const uint32_t* hist, uint64_t* toff, uint64_t* ccoun
     }
   }
 }
+__global__ void k_col_scan(const uint32_t* hist, uint64_t* toff, uint64_t* ccount, uint64_t n_tiles, int P1) {
+  col_scan_body(hist, toff, ccount, n_tiles, P1, blockIdx.x);
+}
+__global__ void k_col_scan_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  col_scan_body(d.b.hist, d.b.toff, d.b.cstart, d.s.n_tiles, 1 << d.s.b1, bid);
+}
 
 // Partition starts and the total number of windows.  One block.
-__global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, Meta* meta) {
+__device__ __forceinline__ void bucket_scan_body(const uint64_t* ccount, uint64_t* cstart, int P1, Meta* meta) {
   extern __shared__ uint64_t sc[];  // [P1]
   __shared__ uint64_t wt[32];
   for (int c = threadIdx.x; c < P1; c += blockDim.x) {
@@ -599,11 +675,18 @@ __global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, 
     meta->n_windows = K;
   }
 }
+__global__ void k_bucket_scan(const uint64_t* ccount, uint64_t* cstart, int P1, Meta* meta) {
+  bucket_scan_body(ccount, cstart, P1, meta);
+}
+__global__ void k_bucket_scan_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  bucket_scan_body(d.b.cstart, d.b.cstart, 1 << d.s.b1, d.b.meta);
+}
 
 // Fine split of every coarse partition, after pass B: the distinct-key estimate (a sampled
 // HyperLogLog filled by pass B) gives the duplication factor K / D, and a fine partition
 // aims at fine_target distinct keys, i.e. fine_target * K / D keys.  One block.
-__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
+__device__ __forceinline__ void fine_plan_body(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
                             uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
   extern __shared__ uint64_t fsc[];  // [P1]
   __shared__ uint64_t wt[32];
@@ -676,6 +759,15 @@ __global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_
     if (NF > nf_max) atomicOr(&meta->status, ST_INTERNAL);
   }
 }
+__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
+                            uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
+  fine_plan_body(cstart, hll, fine_base, fine_m, flo, P1, b1, fine_target, nf_max, meta);
+}
+__global__ void k_fine_plan_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_plan_body(d.b.cstart, d.b.hll, d.b.fine_base, d.b.fine_m, d.b.flo, 1 << d.s.b1, d.s.b1, d.s.fine_target,
+                 (uint32_t)d.s.nf_max, d.b.meta);
+}
 
 // ------------------------------------------------------------------ pass B
 // Per sub-step, NT threads x WPT windows: every key is computed once and kept in registers,
@@ -692,7 +784,7 @@ __device__ __forceinline__ uint64_t key_hash(u128 key) {
 // carried to the staging and the write-out) instead of being recomputed from the key
 // twice; used when two blocks per SM still fit.
 template <int KW, int NT, bool KEEP_C>
-__global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
+__device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, uint32_t bid) {
   typedef typename KeyT<KW>::T K;
   constexpr int WPT = KW == 1 ? 32 : 16;    // windows per thread
   constexpr int TPW = 32 / WPT;             // threads per code word
@@ -714,7 +806,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   __shared__ uint32_t wt[32];
   const int t = threadIdx.x;
   const int wl = t / TPW, h = t % TPW;  // code word of the thread within the sub-step, half
-  const uint64_t tile = blockIdx.x;
+  const uint64_t tile = bid;
   for (int c = t; c < P1; c += NT) {
     cursor[c] = b.cstart[c] + b.toff[tile * P1 + c];
     hist[PAD(c)] = 0;
@@ -820,6 +912,15 @@ __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   for (int i = t; i < kHllRegs; i += NT)
     if (hll_s[i]) atomicMax(&b.hll[i], hll_s[i]);
 }
+template <int KW, int NT, bool KEEP_C>
+__global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
+  scatter_body<KW, NT, KEEP_C>(s, b, blockIdx.x);
+}
+template <int KW, int NT, bool KEEP_C>
+__global__ void __launch_bounds__(NT, 2) k_scatter_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  scatter_body<KW, NT, KEEP_C>(d.s, d.b, bid);
+}
 
 // ------------------------------------------------------------------ phase 2: fine split
 // Fine partition of a key: the coarse field c of u selects {first fine partition of c,
@@ -896,7 +997,7 @@ __device__ __forceinline__ void fetch_bounds(const uint64_t* kbuf, uint64_t c0, 
 }
 
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b) {
+__device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
@@ -907,14 +1008,14 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers 
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
   const uint64_t K_total = min(b.meta->n_windows, s.cap);
-  const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
-  if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
-    fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+  const uint64_t stride = (uint64_t)nblk * kFineChunk;
+  if (threadIdx.x == 0 && bid * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, bid * (uint64_t)kFineChunk, K_total, bnd_s[0]);
     cp_async_wait_all();
   }
   __syncthreads();
   int cur = 0;
-  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
+  for (uint64_t c0 = bid * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
     const uint64_t c1 = min(K_total, c0 + kFineChunk);
     const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
     const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
@@ -947,9 +1048,18 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers 
     __syncthreads();
   }
 }
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b) {
+  fine_hist_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_hist_body<KW>(d.s, d.b, bid, nblk);
+}
 
 // Exclusive scan of the fine histogram (one block of 1024 threads).
-__global__ void k_fine_scan(Shape sh, Buffers b) {
+__device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b) {
   __shared__ uint64_t wt[32];
   __shared__ uint64_t carry_s;
   const uint64_t NF = min(b.meta->n_fine, sh.nf_max);
@@ -999,6 +1109,11 @@ __global__ void k_fine_scan(Shape sh, Buffers b) {
   }
   if (t == 0) b.foff[NF] = carry_s;
 }
+__global__ void k_fine_scan(Shape sh, Buffers b) { fine_scan_body(sh, b); }
+__global__ void k_fine_scan_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_scan_body(d.s, d.b);
+}
 
 // Exclusive scan of in[0, n) into out[0, n) (all threads of the block, n <= 4 * blockDim);
 // returns the total.
@@ -1040,7 +1155,7 @@ __device__ uint32_t block_scan_to(const uint32_t* in, uint32_t* out, int n, uint
 // partition's global cursor once per chunk, stage the keys grouped by fine partition and
 // write every group as one contiguous run.
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b) {
+__device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const int P1 = 1 << s.b1;
@@ -1056,14 +1171,14 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffe
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
   const uint64_t K_total = min(b.meta->n_windows, s.cap);
-  const uint64_t stride = (uint64_t)gridDim.x * kFineChunk;
-  if (threadIdx.x == 0 && blockIdx.x * (uint64_t)kFineChunk < K_total) {
-    fetch_bounds<KW>(b.kbuf, blockIdx.x * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+  const uint64_t stride = (uint64_t)nblk * kFineChunk;
+  if (threadIdx.x == 0 && bid * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, bid * (uint64_t)kFineChunk, K_total, bnd_s[0]);
     cp_async_wait_all();
   }
   __syncthreads();
   int cur = 0;
-  for (uint64_t c0 = blockIdx.x * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
+  for (uint64_t c0 = bid * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
     const uint64_t c1 = min(K_total, c0 + kFineChunk);
     const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
     const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
@@ -1127,6 +1242,15 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffe
     if (threadIdx.x == 0) cp_async_wait_all();
     __syncthreads();
   }
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b) {
+  fine_scatter_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_scatter_body<KW>(d.s, d.b, bid, nblk);
 }
 
 // ------------------------------------------------------------------ phase 2: count + emit
@@ -1599,7 +1723,7 @@ __device__ __forceinline__ void emit_slots(Table<KW> tb, const uint16_t* idx, ui
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
 template <int KW>
-__global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffers b) {
+__device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
   const uint32_t cap_slots = 1u << s.bT_max;
@@ -1869,13 +1993,22 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffer
     }
   }
 }
+template <int KW>
+__global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffers b) {
+  count_emit_body<KW>(s, b);
+}
+template <int KW>
+__global__ void __launch_bounds__(kCountThreads, 1) k_count_emit_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  count_emit_body<KW>(d.s, d.b);
+}
 
 // ------------------------------------------------------------------ final: offsets of the runs
 // Exclusive scan of the distinct counts of the fine partitions (one block of 1024
 // threads): fcur[g] = first output position of partition g, n_distinct = the total.  The
 // look-back words are checked against it, and the deferred partitions are listed (in
 // increasing order) at the front of the spent look-back array for k_compact.
-__global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) {
+__device__ __forceinline__ void scan_distinct_body(const Shape& sh, const Buffers& b) {
   __shared__ uint64_t wt[32];
   __shared__ uint32_t wd[32];
   __shared__ uint64_t carry_s;
@@ -1962,15 +2095,20 @@ __global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) {
     if (dcarry_s != b.meta->n_deferred) atomicOr(&b.meta->status, ST_INTERNAL);
   }
 }
+__global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) { scan_distinct_body(sh, b); }
+__global__ void __launch_bounds__(1024) k_scan_distinct_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  scan_distinct_body(d.s, d.b);
+}
 
 // Move the runs of the deferred fine partitions from their input regions (keys in sbuf,
 // counts in kbuf as 32-bit words) to their output positions: one block per partition.
 template <int KW>
-__global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
+__device__ __forceinline__ void compact_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
   typedef typename KeyT<KW>::T K;
   const uint64_t n_def = min(b.meta->n_deferred, s.nf_max);
   const uint32_t* cnt_src = reinterpret_cast<const uint32_t*>(b.kbuf);
-  for (uint64_t q = blockIdx.x; q < n_def; q += gridDim.x) {
+  for (uint64_t q = bid; q < n_def; q += nblk) {
     const uint64_t g = b.look[q];
     if (g >= min(b.meta->n_fine, s.nf_max)) {
       if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
@@ -1990,8 +2128,18 @@ __global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
     }
   }
 }
+template <int KW>
+__global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
+  compact_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(256) k_compact_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  compact_body<KW>(d.s, d.b, bid, nblk);
+}
 
 // ------------------------------------------------------------------ launches
+constexpr size_t kScatterStaticSmem = 9216;  // pass B's static shared memory (batched form included), rounded up
 static size_t scatter_smem(int kw, int nt, int P1, bool keep_c) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
   return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4 + (keep_c ? sub * 4 : 0);
@@ -2028,6 +2176,20 @@ int configure_kernels(int device) {
   KC_SET(k_count_emit<1>);
   KC_SET(k_count_emit<2>);
   KC_SET(k_bucket_scan);
+  KC_SET(k_pack_count_batch<1>);
+  KC_SET(k_pack_count_batch<2>);
+  KC_SET((k_scatter_batch<1, 256, false>));
+  KC_SET((k_scatter_batch<2, 256, false>));
+  KC_SET((k_scatter_batch<1, 256, true>));
+  KC_SET((k_scatter_batch<2, 256, true>));
+  KC_SET(k_fine_plan_batch);
+  KC_SET(k_fine_hist_batch<1>);
+  KC_SET(k_fine_hist_batch<2>);
+  KC_SET(k_fine_scatter_batch<1>);
+  KC_SET(k_fine_scatter_batch<2>);
+  KC_SET(k_count_emit_batch<1>);
+  KC_SET(k_count_emit_batch<2>);
+  KC_SET(k_bucket_scan_batch);
 #undef KC_SET
   return 0;
 }
@@ -2078,7 +2240,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   KC_STEP("k_bucket_scan");
   if (s.n_tiles > 0) {
     const size_t smB = scatter_smem(s.kw, 256, P1, false), smK = scatter_smem(s.kw, 256, P1, true);
-    if (smB + 8704 > s.smem_budget) return -(int)cudaErrorInvalidConfiguration;
+    if (smB + kScatterStaticSmem > s.smem_budget) return -(int)cudaErrorInvalidConfiguration;
     // keep each window's coarse partition in shared memory if two blocks per SM still fit
     int per_sm = 0;
     if (s.kw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<1, 256, true>, 256, smK);
@@ -2123,6 +2285,117 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   else k_compact<2><<<(unsigned)(n_sms * 8), 256, 0, st>>>(s, b);
   ++launches;
   KC_STEP("k_compact");
+  return launches;
+}
+
+uint32_t batch_blocks(BatchKernel k, const Shape& s, int n_sms, uint64_t bases_total) {
+  auto clampu = [](uint64_t v, uint64_t lo, uint64_t hi) { return (uint32_t)(v < lo ? lo : (v > hi ? hi : v)); };
+  const uint64_t P1 = 1ull << s.b1, nsm = (uint64_t)n_sms;
+  switch (k) {
+    case BK_CLEAR: return clampu((s.nf_max + 2047) / 2048, 1, 32);
+    case BK_CHECK: return clampu((s.n_reads + 255) / 256, 1, 64);
+    case BK_TILE_FIRST: return (uint32_t)((s.n_tiles + 127) / 128);
+    case BK_PACK: return (uint32_t)s.n_tiles;
+    case BK_COL_SCAN: return s.n_tiles ? (uint32_t)((P1 + 31) / 32) : 0u;
+    case BK_SCATTER: return (uint32_t)s.n_tiles;
+    case BK_FINE_HIST:
+    case BK_FINE_SCATTER: return clampu((s.L + 4ull * kFineChunk - 1) / (4ull * kFineChunk), 1, 2 * nsm);
+    case BK_COUNT: {
+      const double share = bases_total ? (double)s.L / (double)bases_total : 1.0;
+      return clampu((uint64_t)(2.0 * (double)nsm * share + 0.999), 1, nsm);
+    }
+    case BK_COMPACT: return clampu(s.nf_max / 8, 1, 8 * nsm);
+    default: return 1u;  // one block per count: bucket scan, fine plan, fine scan, scan of distinct counts
+  }
+}
+
+// The launch sequence of launch_phase1 + launch_phase2, each kernel once for all counts of
+// the batch (all with the same key width); a kernel that gives no count a block is skipped.
+int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mark) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int P1 = bp.P1_max;
+  const Shape& s0 = bp.host[0].s;
+  int launches = 0;
+  auto tab = [&](BatchKernel k) { return BatchTab{bp.desc, bp.blk2s[k], bp.start[k]}; };
+#define KC_BLAUNCH(k, call, name) \
+  if (bp.grid[k]) {               \
+    call;                         \
+    ++launches;                   \
+    KC_STEP(name);                \
+  }
+  KC_BLAUNCH(BK_CLEAR, (k_clear_batch<<<bp.grid[BK_CLEAR], 256, 0, st>>>(tab(BK_CLEAR))), "k_clear_batch");
+  KC_BLAUNCH(BK_CHECK, (k_check_offsets_batch<<<bp.grid[BK_CHECK], 256, 0, st>>>(tab(BK_CHECK))), "k_check_offsets");
+  KC_BLAUNCH(BK_TILE_FIRST, (k_tile_first_batch<<<bp.grid[BK_TILE_FIRST], 128, 0, st>>>(tab(BK_TILE_FIRST))),
+             "k_tile_first");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<1><<<bp.grid[BK_PACK], kPackThreads, (size_t)P1 * 4, st>>>(tab(BK_PACK))),
+               "k_pack_count");
+  } else {
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<2><<<bp.grid[BK_PACK], kPackThreads, (size_t)P1 * 4, st>>>(tab(BK_PACK))),
+               "k_pack_count");
+  }
+  KC_BLAUNCH(BK_COL_SCAN, (k_col_scan_batch<<<bp.grid[BK_COL_SCAN], dim3(32, 32), 0, st>>>(tab(BK_COL_SCAN))),
+             "k_col_scan");
+  KC_BLAUNCH(BK_BUCKET_SCAN,
+             (k_bucket_scan_batch<<<bp.grid[BK_BUCKET_SCAN], 1024, (size_t)P1 * 8, st>>>(tab(BK_BUCKET_SCAN))),
+             "k_bucket_scan");
+  if (bp.grid[BK_SCATTER]) {
+    const size_t smB = scatter_smem(bp.kw, 256, P1, false), smK = scatter_smem(bp.kw, 256, P1, true);
+    if (smB + kScatterStaticSmem > s0.smem_budget) return -(int)cudaErrorInvalidConfiguration;
+    int per_sm = 0;
+    if (bp.kw == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter_batch<1, 256, true>, 256, smK);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter_batch<2, 256, true>, 256, smK);
+    const unsigned g = bp.grid[BK_SCATTER];
+    if (bp.kw == 1) {
+      if (per_sm >= 2) k_scatter_batch<1, 256, true><<<g, 256, smK, st>>>(tab(BK_SCATTER));
+      else k_scatter_batch<1, 256, false><<<g, 256, smB, st>>>(tab(BK_SCATTER));
+    } else {
+      if (per_sm >= 2) k_scatter_batch<2, 256, true><<<g, 256, smK, st>>>(tab(BK_SCATTER));
+      else k_scatter_batch<2, 256, false><<<g, 256, smB, st>>>(tab(BK_SCATTER));
+    }
+    ++launches;
+    KC_STEP("k_scatter");
+  }
+  KC_BLAUNCH(BK_FINE_PLAN, (k_fine_plan_batch<<<bp.grid[BK_FINE_PLAN], 1024, (size_t)P1 * 8, st>>>(tab(BK_FINE_PLAN))),
+             "k_fine_plan");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_FINE_HIST,
+               (k_fine_hist_batch<1><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
+               "k_fine_hist");
+  } else {
+    KC_BLAUNCH(BK_FINE_HIST,
+               (k_fine_hist_batch<2><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
+               "k_fine_hist");
+  }
+  KC_BLAUNCH(BK_FINE_SCAN, (k_fine_scan_batch<<<bp.grid[BK_FINE_SCAN], 1024, 0, st>>>(tab(BK_FINE_SCAN))), "k_fine_scan");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_FINE_SCATTER,
+               (k_fine_scatter_batch<1><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(1, P1), st>>>(
+                   tab(BK_FINE_SCATTER))),
+               "k_fine_scatter");
+  } else {
+    KC_BLAUNCH(BK_FINE_SCATTER,
+               (k_fine_scatter_batch<2><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(2, P1), st>>>(
+                   tab(BK_FINE_SCATTER))),
+               "k_fine_scatter");
+  }
+  const size_t smC = count_kernel_smem(bp.kw, s0.bT_max, s0.tail);
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_COUNT, (k_count_emit_batch<1><<<bp.grid[BK_COUNT], kCountThreads, smC, st>>>(tab(BK_COUNT))),
+               "k_count_emit");
+  } else {
+    KC_BLAUNCH(BK_COUNT, (k_count_emit_batch<2><<<bp.grid[BK_COUNT], kCountThreads, smC, st>>>(tab(BK_COUNT))),
+               "k_count_emit");
+  }
+  KC_BLAUNCH(BK_SCAN_DISTINCT,
+             (k_scan_distinct_batch<<<bp.grid[BK_SCAN_DISTINCT], 1024, 0, st>>>(tab(BK_SCAN_DISTINCT))),
+             "k_scan_distinct");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_COMPACT, (k_compact_batch<1><<<bp.grid[BK_COMPACT], 256, 0, st>>>(tab(BK_COMPACT))), "k_compact");
+  } else {
+    KC_BLAUNCH(BK_COMPACT, (k_compact_batch<2><<<bp.grid[BK_COMPACT], 256, 0, st>>>(tab(BK_COMPACT))), "k_compact");
+  }
+#undef KC_BLAUNCH
   return launches;
 }
 

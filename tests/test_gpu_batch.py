@@ -105,3 +105,32 @@ def test_batch_edge_cases(counter, torch_cuda):
     keys, counts = res.to_numpy()
     res.free()
     assert np.array_equal(keys, ak) and np.array_equal(counts, ac)
+
+
+@pytest.mark.parametrize("k,canonical,defer_all", [(31, True, False), (63, True, False), (21, False, True)])
+def test_batch_several_groups_and_counts_alone(counter, torch_cuda, k, canonical, defer_all):
+    # a 32 MiB arena: the small samples form several groups of batched launches, the larger
+    # ones (scratch above the arena) are counted alone; every result equals kc_count's
+    from paper_2505_04431_gb300 import KmerCounter
+    torch = torch_cuda
+    samples = batch_samples(14, 0.01, seed=2004)
+    samples.insert(5, (np.zeros(0, np.uint8), np.zeros(1, np.uint64)))
+    sizes = [int(o[-1]) for _, o in samples]
+    assert max(sizes) > (5 << 19) and sum(1 for n in sizes if 0 < n < (1 << 20)) >= 3  # ~16 B of scratch per base
+    small = KmerCounter(small_batch_arena=True, defer_all=defer_all)
+    try:
+        dev = [(torch.from_numpy(r).cuda(), o, int(o[-1])) for r, o in samples]
+        results = small.count_batch(dev, k, canonical)
+        order = np.random.RandomState(5).permutation(len(results))  # results freed in any order
+        for i in order:
+            r, o = samples[i]
+            keys, counts = results[i].to_numpy()
+            nv = results[i].n_valid_windows
+            results[i].free()
+            ak, ac, anv = alone(counter, r, o, k, canonical)
+            assert nv == anv and np.array_equal(keys, ak) and np.array_equal(counts, ac), f"sample {i} differs"
+            if sizes[i] < 200_000:
+                ok, oc, onv = oracle.count(r, o, k, canonical)
+                assert onv == nv and np.array_equal(keys, ok) and np.array_equal(counts, oc)
+    finally:
+        small.close()
