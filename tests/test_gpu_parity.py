@@ -353,3 +353,18 @@ def test_full_size_sampled(counter, torch_cuda, name):
         assert total == onv == res.n_valid_windows
     finally:
         res.free()
+
+
+def test_golden_aatgg_repeat(counter):
+    """The paper's heavy-hitter repeat (AATGG)_n, Section IV-D: the GPU path reproduces the
+    closed-form histogram of tests/golden/aatgg_repeat.txt."""
+    from tests.golden import aatgg_repeat
+    reads, offsets, want = aatgg_repeat()
+    for (canonical, k), (wk, wc) in want.items():
+        res = counter.count(reads, offsets, k, canonical)
+        try:
+            keys, counts = res.to_numpy()
+            assert res.n_valid_windows == reads.size - k + 1
+            assert np.array_equal(keys, wk) and np.array_equal(counts, wc), (canonical, k)
+        finally:
+            res.free()

@@ -271,3 +271,15 @@ def test_planted_mistake_is_caught(tmp_path, name):
             if _run(lib, reads, offsets, k, canonical) != brute.sorted_histogram(rs, k, canonical):
                 caught = True
     assert caught, f"pins did not catch planted mistake: {name}"
+
+
+# ---------------------------------------------------------------- golden fixture
+def test_golden_aatgg_repeat():
+    """The paper's heavy-hitter repeat (AATGG)_n, Section IV-D: closed-form histogram."""
+    from tests.golden import aatgg_repeat
+    reads, offsets, want = aatgg_repeat()
+    assert len(want) == 4
+    for (canonical, k), (wk, wc) in want.items():
+        keys, counts, nv = oracle.count(reads, offsets, k, canonical)
+        assert np.array_equal(keys, wk) and np.array_equal(counts, wc), (canonical, k)
+        assert nv == reads.size - k + 1
