@@ -76,6 +76,21 @@ def ncu_traffic(kernel, workload):
     return None
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, elapsed_ms: float) -> float:
+    """Whole-job throughput in G units/s: every rank's units over the slowest rank's time."""
+    return units_per_rank * world * steps / (elapsed_ms / 1e3) / 1e9
+
+
 class Clocks:
     """nvidia-smi samples while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -243,14 +258,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
     ms_per_step = elapsed_ms / args.steps
-    value = K * world * args.steps / (elapsed_ms / 1e3) / 1e9
+    value = whole_job_rate(K, world, args.steps, elapsed_ms)
 
     # end to end through the public API with host buffers: pinned H2D inside the call, D2H of the result
     e2e = None
@@ -278,12 +290,8 @@ def run_ours(args):
         for _ in range(e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": K * world * e2e_steps / dt / 1e9, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": whole_job_rate(K, world, e2e_steps, dt * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(L + 8 * (n_reads + 1)), "d2h_bytes_per_step": int(D * (8 * kw + 4)),
                "steps": e2e_steps}
 
