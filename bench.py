@@ -40,9 +40,11 @@ BATCH_SEED = 1004  # seeds of the batched workload's samples: mix_seed(1004, i)
 WORKLOAD_DESC["serve_2000_requests"] = (
     "2000 count requests, Poisson arrivals at 200/s, k uniform in {21, 31, 63}, read sets of genomes log-uniform "
     "0.05-20 Mbp (times --scale), 150 bp reads, U(10,30)x, 0.5% subst (drawn from a pool of 32 generated read sets); "
-    "served by one plan: requests submitted (kc_submit, queued on the plan's stream) shortest expected first with "
-    "ageing, two in flight, within a device-memory budget, completions polled (kc_job_poll), results kept on the "
-    "device; vs the same in arrival order, rounds of kc_count_batch, and one kc_count per request")
+    "served by one plan: requests taken shortest expected first with ageing (kc_submit, queued on the plan's "
+    "stream, two submissions in flight) within a device-memory budget, completions polled (kc_job_poll), results "
+    "kept on the device; vs the same with continuous batching (waiting requests of the same k and similar size "
+    "submitted together as batched launches, kc_submit_batch), in arrival order, rounds of kc_count_batch, and one "
+    "kc_count per request")
 SERVE_SEED = 1005  # seeds of the served workload: pool read sets mix_seed(1005, i), arrivals RandomState(1005)
 
 
@@ -460,11 +462,13 @@ def run_serve(args):
         res.free()
     # timed: latency to the completion of each count (results stay on the device)
     runs = {}
-    for name in ("served", "served_fifo", "batch_rounds", "plain"):
+    for name in ("served", "served_batched", "served_fifo", "batch_rounds", "plain"):
         reqs = make()
         torch.cuda.synchronize()
         if name == "served":
             info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="sjf")
+        elif name == "served_batched":
+            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="sjf", batch=True)
         elif name == "served_fifo":
             info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="fifo")
         elif name == "batch_rounds":
@@ -474,12 +478,14 @@ def run_serve(args):
         runs[name] = (reqs, info)
     served = runs["served"][0]
     # checked (not timed): every request's result in the mix equals the same count alone
-    for name in ("served", "batch_rounds"):
+    for name in ("served", "served_batched", "batch_rounds"):
         reqs = make()
         for r in reqs:
             r.arrival = 0.0  # all at once: the longest queues
         if name == "served":
             sv.serve_async(counter, reqs, budget, policy="sjf")
+        elif name == "served_batched":
+            sv.serve_async(counter, reqs, budget, policy="sjf", batch=True)
         else:
             sv.serve(counter, reqs, budget)
         mism = [i for i, (r, p_, k_) in enumerate(zip(reqs, picks, ks)) if r.digest != ref[(int(p_), int(k_))]]
@@ -492,7 +498,7 @@ def run_serve(args):
         return {"value": windows / info["makespan"] / 1e9, "unit": UNIT, "ms_per_step": info["makespan"] * 1e3,
                 "latency": sv.latency_summary(reqs)}
 
-    ls, lf, lb, lp = summary("served"), summary("served_fifo"), summary("batch_rounds"), summary("plain")
+    ls, lc, lf, lb, lp = (summary(n) for n in ("served", "served_batched", "served_fifo", "batch_rounds", "plain"))
     line = {"metric": METRIC, "value": ls["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": ls["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64/u128", "data": "synthetic",
@@ -502,7 +508,10 @@ def run_serve(args):
                        "budget_gb": budget / 2**30, "parallelism": "1 GPU",
                        "timing": "host wall clock; latency = arrival to the host seeing the count complete"},
             "latency": ls["latency"], "peak_inflight": runs["served"][1]["peak_inflight"],
-            "policy": "shortest expected service first, with ageing; 2 counts queued on the GPU",
+            "policy": "shortest expected service first, with ageing; 2 submissions queued on the GPU",
+            "served_batched": dict(lc, policy="the same, and the waiting requests of the same k and similar size "
+                                              "in one submission of batched launches (continuous batching)",
+                                   submissions=runs["served_batched"][1]["batches"]),
             "served_fifo": lf, "batch_rounds": lb, "plain": lp,
             "p50_plain_over_served": lp["latency"]["p50_ms"] / ls["latency"]["p50_ms"],
             "p99_plain_over_served": lp["latency"]["p99_ms"] / ls["latency"]["p99_ms"],

@@ -229,6 +229,16 @@ kc_status kc_count_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *cons
 kc_status kc_submit(kc_plan_t plan, const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, uint64_t n_bases,
                     int k, int canonical, uint64_t *job);
 kc_status kc_job_poll(kc_plan_t plan, uint64_t job, kc_result *out, int *done);
+
+/* Submitted batch: the samples of kc_count_batch (same arguments) enqueued on the plan's
+ * stream as kc_count_batch enqueues them (groups of samples sharing batched launches) and
+ * returned at once, one job id per sample in job_ids[i] (collect each with kc_job_poll /
+ * kc_job_wait; the results of a group share buffers released with the last kc_free).
+ * Host arrays and buffers must stay valid until the jobs are collected.  Errors as for
+ * kc_submit; on error no job is created. */
+kc_status kc_submit_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *const *reads,
+                          const uint64_t *const *offsets, const uint64_t *n_reads, const uint64_t *n_bases, int k,
+                          int canonical, uint64_t *job_ids);
 kc_status kc_job_wait(kc_plan_t plan, uint64_t job, kc_result *out);
 
 #ifdef __cplusplus

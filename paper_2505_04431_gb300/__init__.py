@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
             "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch",
-            "kc_submit", "kc_job_poll", "kc_job_wait"]
+            "kc_submit", "kc_job_poll", "kc_job_wait", "kc_submit_batch"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 KC_PLAN_DEFER_ALL = 2
@@ -105,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.kc_job_poll.restype = i32
     lib.kc_job_wait.argtypes = [vp, u64, P(Result)]
     lib.kc_job_wait.restype = i32
+    lib.kc_submit_batch.argtypes = [vp, ctypes.c_uint32, P(vp), P(vp), P(u64), P(u64), i32, i32, P(u64)]
+    lib.kc_submit_batch.restype = i32
     _lib = lib
     return lib
 
@@ -296,6 +298,36 @@ class KmerCounter:
                                               int(bool(canonical)), ctypes.byref(job)))
         self._inflight[job.value] = (rk, ok)
         return job.value
+
+    def submit_batch(self, samples, k: int, canonical: bool = True) -> list[int]:
+        """Enqueue several counts as kc_count_batch would (batched launches) without waiting
+        (kc_submit_batch); one job id per sample, each collected with poll / wait."""
+        n = len(samples)
+        if n == 0:
+            return []
+        keep = []
+        R = (ctypes.c_void_p * n)()
+        O = (ctypes.c_void_p * n)()
+        NR = (ctypes.c_uint64 * n)()
+        NB = (ctypes.c_uint64 * n)()
+        for i, sample in enumerate(samples):
+            reads, offsets = sample[0], sample[1]
+            rp, rk = _ptr(reads)
+            op, ok = _ptr(offsets)
+            keep.append((rk, ok))
+            R[i], O[i] = rp, op
+            NR[i] = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+            if len(sample) > 2:
+                NB[i] = int(sample[2])
+            else:
+                last = offsets[-1]
+                NB[i] = int(last.item() if hasattr(last, "item") else last)
+        jobs = (ctypes.c_uint64 * n)()
+        _check(self._lib, self._lib.kc_submit_batch(self._plan, n, R, O, NR, NB, int(k), int(bool(canonical)), jobs))
+        out = [int(jobs[i]) for i in range(n)]
+        for j, kept in zip(out, keep):
+            self._inflight[j] = kept
+        return out
 
     def poll(self, job: int) -> CountResult | None:
         """The job's result if it has finished (kc_job_poll), else None."""

@@ -69,6 +69,16 @@ struct kc_plan_s {
   size_t btab_bytes = 0;
   void* btab_host = nullptr;
   size_t btab_host_bytes = 0;
+  struct kc::Meta* bmeta = nullptr;  // kc_count_batch: pinned status records
+  uint32_t bmeta_n = 0;
+  // kc_submit_batch: pinned staging of the tables, each buffer reused once its copy is done
+  static constexpr int kStaging = 8;
+  struct Staging {
+    void* host = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;
+  } stg[kStaging];
+  int stg_next = 0;
   // submitted counts (kc_submit): jobs in flight and their pinned status records
   std::unordered_map<uint64_t, AsyncJob*> jobs;
   uint64_t next_job = 1;
@@ -368,18 +378,192 @@ struct AsyncJob {
   Job j;
   int slot = -1;
   cudaEvent_t ev = nullptr;
+  GroupOwner* owner = nullptr;  // a count of a batched group: its results live in the group's buffers
 };
+
+// drop one reference to a group's result buffers (freed with the last)
+void release_owner(kc_plan_s* p, GroupOwner* o) {
+  if (o->refs.fetch_sub(1) == 1) {
+    dev_free(p, o->keys);
+    dev_free(p, o->counts);
+    delete o;
+  }
+}
 
 // release a finished (or failed) job's bookkeeping; with `drop`, its result buffers too
 void retire(kc_plan_s* p, uint64_t id, AsyncJob* a, bool drop) {
   if (drop) {
-    dev_free(p, a->j.okeys);
-    dev_free(p, a->j.ocnts);
+    if (a->owner) {
+      release_owner(p, a->owner);
+    } else {
+      dev_free(p, a->j.okeys);
+      dev_free(p, a->j.ocnts);
+    }
   }
   if (a->ev) cudaEventDestroy(a->ev);
   if (a->slot >= 0) p->pinned_free.push_back(a->slot);
   p->jobs.erase(id);
   delete a;
+}
+
+// ---- batched groups (kc_count_batch, kc_submit_batch)
+struct Group {
+  std::vector<uint32_t> idx;
+  std::vector<size_t> ws_off, key_off, cnt_off;
+  size_t ws = 0, keys = 0, cnts = 0, tab = 0;
+  uint64_t bases = 0;
+};
+struct GroupPlan {
+  std::vector<Group> groups;
+  std::vector<uint32_t> alone;  // counts whose scratch is larger than the arena
+  size_t need_single = 0, arena = 0, tab_total = 0, tab_max = 0, out_total = 0;
+};
+
+// Counts whose scratch fits the arena side by side form a group (taken in order); the
+// table bytes of each group (descriptors, block starts and block-to-count maps).
+bool plan_groups(const kc_plan_s* p, const std::vector<Job>& jobs, GroupPlan& gp, std::string* err) {
+  const size_t arena_cap = p->small_arena ? (32ull << 20)
+                           : p->max_bytes   ? std::max<size_t>(p->max_bytes / 4, 1ull << 28)
+                                            : kBatchArenaBytes;
+  for (uint32_t i = 0; i < (uint32_t)jobs.size(); ++i) {
+    const Job& j = jobs[i];
+    gp.out_total += j.out_key_bytes + j.out_cnt_bytes;
+    const size_t w = align_up(j.ws_bytes, 256);
+    if (w > arena_cap) {
+      gp.alone.push_back(i);
+      gp.need_single = std::max(gp.need_single, j.ws_bytes);
+      continue;
+    }
+    if (gp.groups.empty() || gp.groups.back().ws + w > arena_cap) gp.groups.emplace_back();
+    Group& g = gp.groups.back();
+    g.idx.push_back(i);
+    g.ws_off.push_back(g.ws);
+    g.key_off.push_back(g.keys);
+    g.cnt_off.push_back(g.cnts);
+    g.ws += w;
+    g.keys += align_up(j.out_key_bytes, 256);
+    g.cnts += align_up(j.out_cnt_bytes, 256);
+    g.bases += j.L;
+  }
+  // a group of one count runs alone: the single-count kernels need no tables
+  for (size_t gi = 0; gi < gp.groups.size();) {
+    if (gp.groups[gi].idx.size() == 1) {
+      const uint32_t i = gp.groups[gi].idx[0];
+      gp.alone.push_back(i);
+      gp.need_single = std::max(gp.need_single, jobs[i].ws_bytes);
+      gp.groups.erase(gp.groups.begin() + gi);
+    } else {
+      ++gi;
+    }
+  }
+  for (Group& g : gp.groups) {
+    gp.arena = std::max(gp.arena, g.ws);
+    const uint32_t n = (uint32_t)g.idx.size();
+    size_t words = 0;
+    for (int k = 0; k < kc::BK_N; ++k) {
+      uint64_t sum = 0;
+      for (uint32_t q : g.idx) sum += kc::batch_blocks((kc::BatchKernel)k, jobs[q].s, p->n_sms, g.bases);
+      if (sum > 0x7fffffffull) {
+        *err = "a group needs too many thread blocks";
+        return false;
+      }
+      words += (n + 1) + sum;
+    }
+    g.tab = align_up(n * sizeof(kc::BatchDesc), 256) + align_up(words * 4, 256);
+    gp.tab_total += g.tab;
+    gp.tab_max = std::max(gp.tab_max, g.tab);
+  }
+  return true;
+}
+
+// Enqueue one group on the plan's stream: its outputs (two allocations, owned by `o`), the
+// descriptors and block tables staged at `h` (pinned) and copied to `dv`, the input copies,
+// the batched launches, and each count's status record to meta_dst[q].
+bool enqueue_group(kc_plan_s* p, std::vector<Job>& jobs, const Group& g, GroupOwner* o, uint8_t* h, uint8_t* dv,
+                   kc::Meta* const* meta_dst, uint32_t* launches, kc_status* stc, std::string* err) {
+  const uint32_t n = (uint32_t)g.idx.size();
+  o->keys = dev_alloc(p, g.keys);
+  o->counts = o->keys ? dev_alloc(p, g.cnts) : nullptr;
+  if (!o->keys || !o->counts) {
+    *stc = KC_ENOMEM;
+    *err = "result allocation failed";
+    return false;
+  }
+  kc::BatchDesc* hd = (kc::BatchDesc*)h;
+  int P1_max = 1;
+  for (uint32_t q = 0; q < n; ++q) {
+    Job& j = jobs[g.idx[q]];
+    j.okeys = (uint8_t*)o->keys + g.key_off[q];
+    j.ocnts = (uint8_t*)o->counts + g.cnt_off[q];
+    hd[q].s = j.s;
+    hd[q].b = make_buffers(j, (uint8_t*)p->bws + g.ws_off[q]);
+    P1_max = std::max(P1_max, j.P1);
+    if (!enqueue_copies(j, hd[q].b, p->stream, err)) {
+      *stc = KC_ECUDA;
+      return false;
+    }
+  }
+  kc::BatchPlan bp;
+  bp.n = (int)n;
+  bp.kw = jobs[g.idx[0]].s.kw;
+  bp.P1_max = P1_max;
+  bp.host = hd;
+  bp.desc = (const kc::BatchDesc*)dv;
+  const size_t dbytes = align_up(n * sizeof(kc::BatchDesc), 256);
+  uint32_t* hw = (uint32_t*)(h + dbytes);
+  const uint32_t* dw = (const uint32_t*)(dv + dbytes);
+  for (int k = 0; k < kc::BK_N; ++k) {
+    uint32_t* start = hw;
+    uint32_t* blk2s = hw + n + 1;
+    uint32_t at = 0;
+    for (uint32_t q = 0; q < n; ++q) {
+      start[q] = at;
+      const uint32_t c = kc::batch_blocks((kc::BatchKernel)k, jobs[g.idx[q]].s, p->n_sms, g.bases);
+      for (uint32_t x = 0; x < c; ++x) blk2s[at + x] = q;
+      at += c;
+    }
+    start[n] = at;
+    bp.start[k] = dw;
+    bp.blk2s[k] = dw + n + 1;
+    bp.grid[k] = at;
+    hw += n + 1 + at;
+    dw += n + 1 + at;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dv, h, g.tab, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess) {
+    *stc = KC_ECUDA;
+    *err = std::string("copying tables: ") + cudaGetErrorString(e);
+    return false;
+  }
+  const kc::Marker none;
+  const int nl = kc::launch_batch(bp, p->n_sms, (void*)p->stream, none);
+  if (nl < 0) {
+    *stc = KC_ECUDA;
+    *err = std::string("launch: ") + cudaGetErrorString((cudaError_t)(-nl));
+    return false;
+  }
+  *launches += (uint32_t)nl;
+  for (uint32_t q = 0; q < n; ++q)
+    if ((e = cudaMemcpyAsync(meta_dst[q], hd[q].b.meta, sizeof(kc::Meta), cudaMemcpyDeviceToHost, p->stream)) !=
+        cudaSuccess) {
+      *stc = KC_ECUDA;
+      *err = cudaGetErrorString(e);
+      return false;
+    }
+  return true;
+}
+
+// grow a plan-held device buffer (stream-ordered: earlier work on the plan's stream keeps
+// the old one until it is done)
+bool grow_dev(kc_plan_s* p, void*& buf, size_t& have, size_t want) {
+  if (have >= want) return true;
+  dev_free(p, buf);
+  buf = nullptr;
+  have = 0;
+  buf = dev_alloc(p, want);
+  if (!buf) return false;
+  have = want;
+  return true;
 }
 
 void record_stats(kc_plan_s* p, const Job& j, const kc::Meta& m) {
@@ -458,6 +642,11 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   }
   if (p->pinned) cudaFreeHost(p->pinned);
   if (p->btab_host) cudaFreeHost(p->btab_host);
+  if (p->bmeta) cudaFreeHost(p->bmeta);
+  for (auto& st : p->stg) {
+    if (st.ev) cudaEventDestroy(st.ev);
+    if (st.host) cudaFreeHost(st.host);
+  }
   dev_free(p, p->bws);
   dev_free(p, p->btab);
   dev_free(p, p->ws);
@@ -473,12 +662,7 @@ kc_status kc_free(kc_plan_t p, kc_result* r) {
   if (!p || !r) return fail(KC_EINVAL, "kc_free: NULL argument");
   cudaSetDevice(p->device);
   if (r->_owner) {  // a result of a batched group: the group's buffers go with its last result
-    GroupOwner* o = (GroupOwner*)r->_owner;
-    if (o->refs.fetch_sub(1) == 1) {
-      dev_free(p, o->keys);
-      dev_free(p, o->counts);
-      delete o;
-    }
+    release_owner(p, (GroupOwner*)r->_owner);
   } else {
     dev_free(p, r->keys);
     dev_free(p, r->counts);
@@ -640,85 +824,39 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
   }
   // ---- groups: counts whose scratch fits the arena together share the batched launches
   // (every kernel once per group); a count larger than the arena runs alone
-  const size_t arena_cap = p->small_arena ? (32ull << 20)
-                           : p->max_bytes   ? std::max<size_t>(p->max_bytes / 4, 1ull << 28)
-                                            : kBatchArenaBytes;
-  struct Group {
-    std::vector<uint32_t> idx;
-    std::vector<size_t> ws_off, key_off, cnt_off;
-    size_t ws = 0, keys = 0, cnts = 0, tab = 0;
-    uint64_t bases = 0;
-    uint32_t grid[kc::BK_N] = {};
-  };
-  std::vector<Group> groups;
-  std::vector<uint32_t> alone;
-  size_t need_single = 0, arena = 0, total = 0, tab_total = 0;
-  for (uint32_t i = 0; i < n_samples; ++i) {
-    const Job& j = jobs[i];
-    total += j.out_key_bytes + j.out_cnt_bytes;
-    const size_t w = align_up(j.ws_bytes, 256);
-    if (w > arena_cap) {
-      alone.push_back(i);
-      need_single = std::max(need_single, j.ws_bytes);
-      continue;
-    }
-    if (groups.empty() || groups.back().ws + w > arena_cap) groups.emplace_back();
-    Group& g = groups.back();
-    g.idx.push_back(i);
-    g.ws_off.push_back(g.ws);
-    g.key_off.push_back(g.keys);
-    g.cnt_off.push_back(g.cnts);
-    g.ws += w;
-    g.keys += align_up(j.out_key_bytes, 256);
-    g.cnts += align_up(j.out_cnt_bytes, 256);
-    g.bases += j.L;
-  }
-  for (Group& g : groups) {
-    arena = std::max(arena, g.ws);
-    const uint32_t n = (uint32_t)g.idx.size();
-    size_t words = 0;
-    for (int k = 0; k < kc::BK_N; ++k) {
-      uint64_t sum = 0;
-      for (uint32_t q : g.idx) sum += kc::batch_blocks((kc::BatchKernel)k, jobs[q].s, p->n_sms, g.bases);
-      if (sum > 0x7fffffffull) return fail(KC_EINVAL, "kc_count_batch: a group needs too many thread blocks");
-      g.grid[k] = (uint32_t)sum;
-      words += (n + 1) + sum;
-    }
-    g.tab = align_up(n * sizeof(kc::BatchDesc), 256) + align_up(words * 4, 256);
-    tab_total += g.tab;
-  }
-  total += arena + need_single + tab_total;
+  GroupPlan gp;
+  std::string err;
+  if (!plan_groups(p, jobs, gp, &err)) return fail(KC_EINVAL, "kc_count_batch: " + err);
+  const size_t total = gp.out_total + gp.arena + gp.need_single + gp.tab_total;
   if (p->max_bytes && total > p->max_bytes)
     return fail(KC_ENOMEM, "kc_count_batch: the batch needs more device memory than max_device_bytes");
-  auto grow = [&](void*& buf, size_t& have, size_t want) {
-    if (have >= want) return true;
-    dev_free(p, buf);
-    buf = nullptr;
-    have = 0;
-    buf = dev_alloc(p, want);
-    if (!buf) return false;
-    have = want;
-    return true;
-  };
-  if (!alone.empty() && !grow(p->ws, p->ws_bytes, need_single))
+  if (!gp.alone.empty() && !grow_dev(p, p->ws, p->ws_bytes, gp.need_single))
     return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
-  if (!groups.empty() && (!grow(p->bws, p->bws_bytes, arena) || !grow(p->btab, p->btab_bytes, tab_total)))
+  if (!gp.groups.empty() &&
+      (!grow_dev(p, p->bws, p->bws_bytes, gp.arena) || !grow_dev(p, p->btab, p->btab_bytes, gp.tab_total)))
     return fail(KC_ENOMEM, "kc_count_batch: scratch allocation failed");
-  if (p->btab_host_bytes < tab_total) {
+  if (p->btab_host_bytes < gp.tab_total) {
     if (p->btab_host) cudaFreeHost(p->btab_host);
     p->btab_host = nullptr;
     p->btab_host_bytes = 0;
-    if ((e = cudaMallocHost(&p->btab_host, tab_total)) != cudaSuccess) return cuda_fail(e, "kc_count_batch: pinned tables");
-    p->btab_host_bytes = tab_total;
+    if ((e = cudaMallocHost(&p->btab_host, gp.tab_total)) != cudaSuccess)
+      return cuda_fail(e, "kc_count_batch: pinned tables");
+    p->btab_host_bytes = gp.tab_total;
   }
-  kc::Meta* metas = nullptr;
-  if ((e = cudaMallocHost((void**)&metas, sizeof(kc::Meta) * n_samples)) != cudaSuccess)
-    return cuda_fail(e, "kc_count_batch: pinned status buffer");
-  std::vector<GroupOwner*> owners(groups.size(), nullptr);
+  if (p->bmeta_n < n_samples) {
+    if (p->bmeta) cudaFreeHost(p->bmeta);
+    p->bmeta = nullptr;
+    p->bmeta_n = 0;
+    if ((e = cudaMallocHost((void**)&p->bmeta, sizeof(kc::Meta) * n_samples)) != cudaSuccess)
+      return cuda_fail(e, "kc_count_batch: pinned status buffer");
+    p->bmeta_n = n_samples;
+  }
+  kc::Meta* metas = p->bmeta;
+  std::vector<GroupOwner*> owners(gp.groups.size(), nullptr);
   auto release = [&](kc_status stc, const std::string& msg) {
     cudaStreamSynchronize(p->stream);
     cudaGetLastError();
-    for (uint32_t i : alone) {
+    for (uint32_t i : gp.alone) {
       dev_free(p, jobs[i].okeys);
       dev_free(p, jobs[i].ocnts);
     }
@@ -729,14 +867,12 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
         delete o;
       }
     for (uint32_t i = 0; i < n_samples; ++i) memset(&out[i], 0, sizeof(out[i]));
-    cudaFreeHost(metas);
     return fail(stc, msg);
   };
   // ---- enqueue everything on the plan's stream; no host synchronisation until the end
   const kc::Marker none;
   uint32_t launches = 0;
-  std::string err;
-  for (uint32_t i : alone) {
+  for (uint32_t i : gp.alone) {
     Job& j = jobs[i];
     j.okeys = dev_alloc(p, j.out_key_bytes);
     j.ocnts = j.okeys ? dev_alloc(p, j.out_cnt_bytes) : nullptr;
@@ -747,63 +883,16 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     launches += (uint32_t)nl;
   }
   size_t tab_at = 0;
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    Group& g = groups[gi];
-    const uint32_t n = (uint32_t)g.idx.size();
-    GroupOwner* o = new GroupOwner();
-    owners[gi] = o;
-    o->keys = dev_alloc(p, g.keys);
-    o->counts = o->keys ? dev_alloc(p, g.cnts) : nullptr;
-    if (!o->keys || !o->counts) return release(KC_ENOMEM, "kc_count_batch: result allocation failed");
-    o->refs = (int)n;
-    // descriptors and block tables, staged in pinned memory and copied in one piece
-    uint8_t* h = (uint8_t*)p->btab_host + tab_at;
-    uint8_t* dv = (uint8_t*)p->btab + tab_at;
-    kc::BatchDesc* hd = (kc::BatchDesc*)h;
-    int P1_max = 1;
-    for (uint32_t q = 0; q < n; ++q) {
-      Job& j = jobs[g.idx[q]];
-      j.okeys = (uint8_t*)o->keys + g.key_off[q];
-      j.ocnts = (uint8_t*)o->counts + g.cnt_off[q];
-      hd[q].s = j.s;
-      hd[q].b = make_buffers(j, (uint8_t*)p->bws + g.ws_off[q]);
-      P1_max = std::max(P1_max, j.P1);
-      if (!enqueue_copies(j, hd[q].b, p->stream, &err)) return release(KC_ECUDA, "kc_count_batch: " + err);
-    }
-    kc::BatchPlan bp;
-    bp.n = (int)n;
-    bp.kw = jobs[g.idx[0]].s.kw;
-    bp.P1_max = P1_max;
-    bp.host = hd;
-    bp.desc = (const kc::BatchDesc*)dv;
-    uint32_t* hw = (uint32_t*)(h + align_up(n * sizeof(kc::BatchDesc), 256));
-    const uint32_t* dw = (const uint32_t*)(dv + align_up(n * sizeof(kc::BatchDesc), 256));
-    for (int k = 0; k < kc::BK_N; ++k) {
-      uint32_t* start = hw;
-      uint32_t* blk2s = hw + n + 1;
-      uint32_t at = 0;
-      for (uint32_t q = 0; q < n; ++q) {
-        start[q] = at;
-        const uint32_t c = kc::batch_blocks((kc::BatchKernel)k, jobs[g.idx[q]].s, p->n_sms, g.bases);
-        for (uint32_t x = 0; x < c; ++x) blk2s[at + x] = q;
-        at += c;
-      }
-      start[n] = at;
-      bp.start[k] = dw;
-      bp.blk2s[k] = dw + n + 1;
-      bp.grid[k] = at;
-      hw += n + 1 + at;
-      dw += n + 1 + at;
-    }
-    if ((e = cudaMemcpyAsync(dv, h, g.tab, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
-      return release(KC_ECUDA, std::string("kc_count_batch: copying tables: ") + cudaGetErrorString(e));
-    const int nl = kc::launch_batch(bp, p->n_sms, (void*)p->stream, none);
-    if (nl < 0) return release(KC_ECUDA, std::string("kc_count_batch: launch: ") + cudaGetErrorString((cudaError_t)(-nl)));
-    launches += (uint32_t)nl;
-    for (uint32_t q = 0; q < n; ++q)
-      if ((e = cudaMemcpyAsync(&metas[g.idx[q]], hd[q].b.meta, sizeof(kc::Meta), cudaMemcpyDeviceToHost, p->stream)) !=
-          cudaSuccess)
-        return release(KC_ECUDA, std::string("kc_count_batch: ") + cudaGetErrorString(e));
+  for (size_t gi = 0; gi < gp.groups.size(); ++gi) {
+    const Group& g = gp.groups[gi];
+    owners[gi] = new GroupOwner();
+    owners[gi]->refs = (int)g.idx.size();
+    std::vector<kc::Meta*> dst(g.idx.size());
+    for (size_t q = 0; q < g.idx.size(); ++q) dst[q] = &metas[g.idx[q]];
+    kc_status stc = KC_OK;
+    if (!enqueue_group(p, jobs, g, owners[gi], (uint8_t*)p->btab_host + tab_at, (uint8_t*)p->btab + tab_at, dst.data(),
+                       &launches, &stc, &err))
+      return release(stc, "kc_count_batch: " + err);
     tab_at += g.tab;
   }
   if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess)
@@ -814,11 +903,10 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     if (stc != KC_OK) return release(stc, msg + " (sample " + std::to_string(i) + ")");
   }
   for (uint32_t i = 0; i < n_samples; ++i) fill_result(jobs[i], metas[i], &out[i]);
-  for (size_t gi = 0; gi < groups.size(); ++gi)
-    for (uint32_t q : groups[gi].idx) out[q]._owner = owners[gi];
+  for (size_t gi = 0; gi < gp.groups.size(); ++gi)
+    for (uint32_t q : gp.groups[gi].idx) out[q]._owner = owners[gi];
   p->stats = kc_stats{};
   p->stats.kernel_launches = launches;
-  cudaFreeHost(metas);
   return KC_OK;
 }
 
@@ -898,6 +986,129 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   return KC_OK;
 }
 
+
+kc_status kc_submit_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* reads, const uint64_t* const* offsets,
+                          const uint64_t* n_reads, const uint64_t* n_bases, int k, int canonical, uint64_t* job_ids) {
+  g_err.clear();
+  if (!p || !job_ids) return fail(KC_EINVAL, "kc_submit_batch: plan and job_ids must not be NULL");
+  for (uint32_t i = 0; i < n_samples; ++i) job_ids[i] = 0;
+  if (n_samples == 0) return KC_OK;
+  if (!reads || !offsets || !n_reads || !n_bases) return fail(KC_EINVAL, "kc_submit_batch: NULL sample array");
+  if (k < 1 || k > 64) return fail(KC_EINVAL, "kc_submit_batch: k must be in 1..64");
+  ScopedBusy busy(p);
+  if (!busy.ok) return fail(KC_EBUSY, "kc_submit_batch: plan in use by another call");
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  std::vector<Job> jobs(n_samples);
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    if (!offsets[i]) return fail(KC_EINVAL, "kc_submit_batch: offsets of a sample is NULL");
+    const bool off_dev = is_device_ptr(offsets[i]);
+    if (!off_dev) {
+      if (offsets[i][0] != 0 || offsets[i][n_reads[i]] != n_bases[i])
+        return fail(KC_EINVAL, "kc_submit_batch: a sample's offsets must run from 0 to its base count");
+      for (uint64_t r = 0; r < n_reads[i]; ++r)
+        if (offsets[i][r + 1] < offsets[i][r]) return fail(KC_EINVAL, "kc_submit_batch: offsets must be non-decreasing");
+    }
+    if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_submit_batch: reads of a sample is NULL");
+    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
+  }
+  GroupPlan gp;
+  std::string err;
+  if (!plan_groups(p, jobs, gp, &err)) return fail(KC_EINVAL, "kc_submit_batch: " + err);
+  if (p->max_bytes && gp.out_total + gp.arena + gp.need_single + gp.tab_max > p->max_bytes)
+    return fail(KC_ENOMEM, "kc_submit_batch: the batch needs more device memory than max_device_bytes");
+  if (!p->pinned) {
+    if ((e = cudaMallocHost((void**)&p->pinned, sizeof(kc::Meta) * kc_plan_s::kPinned)) != cudaSuccess)
+      return cuda_fail(e, "kc_submit_batch: pinned status records");
+    for (int i = kc_plan_s::kPinned - 1; i >= 0; --i) p->pinned_free.push_back(i);
+  }
+  if (p->pinned_free.size() < n_samples) return fail(KC_EBUSY, "kc_submit_batch: too many counts in flight");
+  // scratch, arena and device tables grow in stream order (earlier counts keep the old ones)
+  if (!gp.alone.empty() && !grow_dev(p, p->ws, p->ws_bytes, gp.need_single))
+    return fail(KC_ENOMEM, "kc_submit_batch: scratch allocation failed");
+  if (!gp.groups.empty() &&
+      (!grow_dev(p, p->bws, p->bws_bytes, gp.arena) || !grow_dev(p, p->btab, p->btab_bytes, gp.tab_max)))
+    return fail(KC_ENOMEM, "kc_submit_batch: scratch allocation failed");
+  // one job per count, each with its pinned status slot and completion event
+  std::vector<AsyncJob*> made(n_samples, nullptr);
+  std::vector<uint64_t> ids(n_samples, 0);
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    AsyncJob* a = new AsyncJob();
+    a->slot = p->pinned_free.back();
+    p->pinned_free.pop_back();
+    ids[i] = p->next_job++;
+    p->jobs[ids[i]] = a;
+    made[i] = a;
+  }
+  std::vector<GroupOwner*> owners(gp.groups.size(), nullptr);
+  auto release = [&](kc_status stc, const std::string& msg) {
+    cudaStreamSynchronize(p->stream);
+    cudaGetLastError();
+    for (uint32_t i : gp.alone) {
+      dev_free(p, jobs[i].okeys);
+      dev_free(p, jobs[i].ocnts);
+    }
+    for (GroupOwner* o : owners)
+      if (o) {
+        dev_free(p, o->keys);
+        dev_free(p, o->counts);
+        delete o;
+      }
+    for (uint32_t i = 0; i < n_samples; ++i) retire(p, ids[i], made[i], false);  // no buffers of their own yet
+    return fail(stc, msg);
+  };
+  const kc::Marker none;
+  uint32_t launches = 0;
+  for (uint32_t i : gp.alone) {
+    Job& j = jobs[i];
+    j.okeys = dev_alloc(p, j.out_key_bytes);
+    j.ocnts = j.okeys ? dev_alloc(p, j.out_cnt_bytes) : nullptr;
+    if (!j.okeys || !j.ocnts) return release(KC_ENOMEM, "kc_submit_batch: result allocation failed");
+    int nl = 0;
+    if (!enqueue_job(j, (uint8_t*)p->ws, p->stream, &p->pinned[made[i]->slot], none, p->n_sms, &nl, &err))
+      return release(KC_ECUDA, "kc_submit_batch: " + err);
+    launches += (uint32_t)nl;
+  }
+  for (size_t gi = 0; gi < gp.groups.size(); ++gi) {
+    const Group& g = gp.groups[gi];
+    // a pinned staging buffer whose last copy has completed
+    kc_plan_s::Staging& st = p->stg[p->stg_next];
+    p->stg_next = (p->stg_next + 1) % kc_plan_s::kStaging;
+    if (st.ev && (e = cudaEventSynchronize(st.ev)) != cudaSuccess)
+      return release(KC_ECUDA, std::string("kc_submit_batch: ") + cudaGetErrorString(e));
+    if (st.bytes < g.tab) {
+      if (st.host) cudaFreeHost(st.host);
+      st.host = nullptr;
+      st.bytes = 0;
+      if ((e = cudaMallocHost(&st.host, g.tab)) != cudaSuccess)
+        return release(KC_ECUDA, std::string("kc_submit_batch: pinned tables: ") + cudaGetErrorString(e));
+      st.bytes = g.tab;
+    }
+    if (!st.ev && (e = cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming)) != cudaSuccess)
+      return release(KC_ECUDA, std::string("kc_submit_batch: ") + cudaGetErrorString(e));
+    owners[gi] = new GroupOwner();
+    owners[gi]->refs = (int)g.idx.size();
+    std::vector<kc::Meta*> dst(g.idx.size());
+    for (size_t q = 0; q < g.idx.size(); ++q) dst[q] = &p->pinned[made[g.idx[q]]->slot];
+    kc_status stc = KC_OK;
+    if (!enqueue_group(p, jobs, g, owners[gi], (uint8_t*)st.host, (uint8_t*)p->btab, dst.data(), &launches, &stc, &err))
+      return release(stc, "kc_submit_batch: " + err);
+    if ((e = cudaEventRecord(st.ev, p->stream)) != cudaSuccess)
+      return release(KC_ECUDA, std::string("kc_submit_batch: ") + cudaGetErrorString(e));
+  }
+  for (uint32_t i = 0; i < n_samples; ++i) {
+    if ((e = cudaEventCreateWithFlags(&made[i]->ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(made[i]->ev, p->stream)) != cudaSuccess)
+      return release(KC_ECUDA, std::string("kc_submit_batch: completion event: ") + cudaGetErrorString(e));
+  }
+  // hand over: each job owns its outputs (counted alone) or a reference on its group's buffers
+  for (uint32_t i = 0; i < n_samples; ++i) made[i]->j = jobs[i];
+  for (size_t gi = 0; gi < gp.groups.size(); ++gi)
+    for (uint32_t q : gp.groups[gi].idx) made[q]->owner = owners[gi];
+  for (uint32_t i = 0; i < n_samples; ++i) job_ids[i] = ids[i];
+  return KC_OK;
+}
+
 static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done, bool block) {
   g_err.clear();
   if (!p || !out || !done) return fail(KC_EINVAL, "kc_job_poll: NULL argument");
@@ -925,6 +1136,7 @@ static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done
   }
   memset(out, 0, sizeof(*out));
   fill_result(a->j, m, out);
+  out->_owner = a->owner;  // the result keeps the job's reference on the group's buffers
   record_stats(p, a->j, m);
   retire(p, id, a, false);
   return KC_OK;

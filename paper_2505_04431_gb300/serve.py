@@ -72,49 +72,80 @@ def expected_seconds(req: Request) -> float:
 
 
 def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: bool = True,
-                keep_digest: bool = True, idle_sleep: float = 50e-6, policy: str = "fifo", depth: int | None = None):
+                keep_digest: bool = True, idle_sleep: float = 50e-6, policy: str = "fifo", depth: int | None = None,
+                batch: bool = False, max_batch: int = 64, batch_ratio: float = 4.0):
     """Submit arrived requests while the footprints of the requests in flight stay within the
-    budget (and, with `depth`, while fewer than `depth` are in flight); collect results as
-    they complete.  One request is always admitted when none is in flight, whatever its
-    footprint.  policy "fifo" submits in arrival order; "sjf" submits next the waiting
-    request with the least expected service time minus the time it has waited (shortest
-    first, with ageing so that a large request is not held back for ever); "sjf" defaults
-    to depth 2, so that the GPU always has the next count queued."""
+    budget (and, with `depth`, while fewer than `depth` submissions are in flight); collect
+    results as they complete.  One request is always admitted when none is in flight,
+    whatever its footprint.  policy "fifo" takes the waiting requests in arrival order;
+    "sjf" takes next the one with the least expected service time minus the time it has
+    waited (shortest first, with ageing so that a large request is not held back for ever),
+    and defaults to depth 2, so that the GPU always has the next submission queued.  With
+    `batch` (continuous batching), the waiting requests with the same k whose expected
+    service time is at most `batch_ratio` times that of the request taken (or under 1 ms)
+    join it, in policy order and within the budget, in one submission of batched launches
+    (kc_submit_batch, at most `max_batch` requests)."""
     if policy not in ("fifo", "sjf"):
         raise ValueError(f"unknown policy {policy!r}")
     if depth is None and policy == "sjf":
         depth = 2
     queue = collections.deque(sorted(requests, key=lambda r: r.arrival))
     waiting: list = []
-    inflight: dict = {}  # job id -> (request, footprint)
+    inflight: dict = {}  # job id -> (request, footprint, submission)
+    open_subs: dict = {}  # submission -> its jobs still in flight
+    next_sub = 0
     used = 0
     peak_inflight = 0
+    submissions = 0
     t0 = time.perf_counter()
     while queue or waiting or inflight:
         now = time.perf_counter() - t0
         while queue and queue[0].arrival <= now:
             waiting.append(queue.popleft())
-        while waiting and (depth is None or len(inflight) < depth):
+        while waiting and (depth is None or len(open_subs) < depth):
             if policy == "sjf":
-                i = min(range(len(waiting)), key=lambda q: expected_seconds(waiting[q]) - (now - waiting[q].arrival))
+                prio = lambda q: expected_seconds(waiting[q]) - (now - waiting[q].arrival)  # noqa: E731
             else:
-                i = 0
+                prio = lambda q: q  # noqa: E731
+            i = min(range(len(waiting)), key=prio)
             r = waiting[i]
             f = footprint(r)
             if inflight and used + f > budget_bytes:
                 break
-            job = counter.submit(r.reads, r.offsets, r.k, canonical, n_bases=r.n_bases)
-            inflight[job] = (r, f)
-            used += f
-            waiting.pop(i)
+            group, tot = [i], used + f
+            if batch:
+                cap = max(batch_ratio * expected_seconds(r), 1e-3)
+                for q in sorted((q for q in range(len(waiting)) if q != i and waiting[q].k == r.k), key=prio):
+                    if len(group) >= max_batch:
+                        break
+                    fq = footprint(waiting[q])
+                    if expected_seconds(waiting[q]) <= cap and tot + fq <= budget_bytes:
+                        group.append(q)
+                        tot += fq
+            reqs = [waiting[q] for q in group]
+            if len(reqs) == 1:
+                jobs = [counter.submit(r.reads, r.offsets, r.k, canonical, n_bases=r.n_bases)]
+            else:
+                jobs = counter.submit_batch([(x.reads, x.offsets, x.n_bases) for x in reqs], r.k, canonical)
+            open_subs[next_sub] = len(jobs)
+            for job, x in zip(jobs, reqs):
+                inflight[job] = (x, footprint(x), next_sub)
+            next_sub += 1
+            submissions += 1
+            used = tot
+            for q in sorted(group, reverse=True):
+                waiting.pop(q)
         peak_inflight = max(peak_inflight, len(inflight))
         progressed = False
         for job in list(inflight):
             res = counter.poll(job)
             if res is None:
                 continue
-            r, f = inflight.pop(job)
+            r, f, sub = inflight.pop(job)
             used -= f
+            open_subs[sub] -= 1
+            if not open_subs[sub]:
+                del open_subs[sub]
             _finish(r, res, time.perf_counter() - t0, keep_digest)
             progressed = True
         if not progressed:
@@ -122,7 +153,7 @@ def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: 
                 time.sleep(max(0.0, min(queue[0].arrival - (time.perf_counter() - t0), 0.002)))
             else:
                 time.sleep(idle_sleep)
-    return {"batches": len(requests), "peak_inflight": peak_inflight, "makespan": time.perf_counter() - t0}
+    return {"batches": submissions, "peak_inflight": peak_inflight, "makespan": time.perf_counter() - t0}
 
 
 def serve(counter, requests: list[Request], budget_bytes: int, canonical: bool = True, keep_digest: bool = True):

@@ -160,3 +160,56 @@ def test_served_batches_identical_to_single_counts(counter, torch_cuda):
     info = sv.serve(counter, reqs, budget_bytes=2 << 30)
     assert info["batches"] < len(reqs)  # requests were batched
     assert [r.digest for r in reqs] == digests_alone(counter, reqs)
+
+
+def test_submit_batch_matches_single_counts(counter, torch_cuda):
+    # a 32 MiB arena: several groups of batched launches and counts alone in one submission;
+    # two submissions queued before anything is collected, collected out of order
+    from paper_2505_04431_gb300 import KC_EINVAL, KcError, KmerCounter
+    torch = torch_cuda
+    inputs = []
+    for i in range(9):
+        r, o, _ = synth.generate(synth.SERVE, synth.mix_seed(3005, i), 0.02)
+        inputs.append((r, o))
+    inputs.insert(2, (np.zeros(0, np.uint8), np.zeros(1, np.uint64)))
+    small = KmerCounter(small_batch_arena=True)
+    try:
+        dev = [(torch.from_numpy(r).cuda(), torch.from_numpy(o.view(np.int64)).cuda(), int(o[-1])) for r, o in inputs]
+        torch.cuda.synchronize()
+        with pytest.raises(KcError) as e:  # bad host offsets: refused, no job
+            bad = inputs[0][1].copy()
+            bad[1], bad[2] = bad[2], bad[1]
+            small.submit_batch([dev[1], (dev[0][0], bad, int(bad[-1]))], 31)
+        assert e.value.status == KC_EINVAL
+        jobs31 = small.submit_batch(dev[:6], 31)
+        jobs63 = small.submit_batch(dev[4:], 63)
+        want = [(i, 31, j) for i, j in enumerate(jobs31)] + [(4 + i, 63, j) for i, j in enumerate(jobs63)]
+        got = {}
+        for i, k, j in reversed(want):
+            if j % 2:
+                got[j] = small.wait(j)
+            else:
+                t_end = time.time() + 60
+                while (res := small.poll(j)) is None:
+                    assert time.time() < t_end
+                    time.sleep(1e-3)
+                got[j] = res
+        for i, k, j in want:
+            res = got[j]
+            keys, counts = res.to_numpy()
+            nv = res.n_valid_windows
+            r, o = inputs[i]
+            ak, ac, anv = alone(counter, r, o, k)
+            assert nv == anv and np.array_equal(keys, ak) and np.array_equal(counts, ac), f"input {i}, k {k}"
+        for j in np.random.RandomState(3).permutation([j for _, _, j in want]):
+            got[int(j)].free()
+    finally:
+        small.close()
+
+
+def test_served_async_batched_identical_to_single_counts(counter, torch_cuda):
+    from paper_2505_04431_gb300 import serve as sv
+    reqs = make_requests(torch_cuda, n=60, seed=9)
+    info = sv.serve_async(counter, reqs, budget_bytes=2 << 30, policy="sjf", batch=True)
+    assert info["batches"] < len(reqs)  # some requests shared a submission
+    assert [r.digest for r in reqs] == digests_alone(counter, reqs)

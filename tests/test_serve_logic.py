@@ -78,6 +78,7 @@ class FakeAsyncCounter:
         self.spb = seconds_per_base
         self.jobs = {}
         self.submitted = []
+        self.batches = []
         self.submit_times = []
         self.max_inflight = 0
         self.next = 1
@@ -91,6 +92,20 @@ class FakeAsyncCounter:
         self.submit_times.append(time.perf_counter())
         self.max_inflight = max(self.max_inflight, len(self.jobs))
         return jid
+
+    def submit_batch(self, samples, k, canonical=True):
+        import time
+        self.batches.append((k, [sm[2] for sm in samples]))
+        t_end = time.perf_counter() + self.spb * sum(sm[2] for sm in samples)
+        out = []
+        for sm in samples:
+            jid = self.next
+            self.next += 1
+            self.jobs[jid] = (t_end, sm[2])  # a batch completes as a whole
+            self.submitted.append((k, sm[2]))
+            out.append(jid)
+        self.max_inflight = max(self.max_inflight, len(self.jobs))
+        return out
 
     def poll(self, job):
         import time
@@ -157,3 +172,35 @@ def test_async_sjf_ageing_lets_a_long_waiting_request_through():
     assert sv.expected_seconds(long_wait) - waiting_since < sv.expected_seconds(fresh) - 0.0
     with pytest.raises(ValueError):
         sv.serve_async(c, [fresh], budget_bytes=1, keep_digest=False, policy="lifo")
+
+
+def test_async_batching_groups_waiting_requests_of_one_k():
+    # a long count occupies the GPU (depth 1); meanwhile small requests of two k values
+    # arrive; they go in one batched submission per k, the k = 63 ones apart, and one
+    # request far larger than the others stays out of their batch
+    c = FakeAsyncCounter(seconds_per_base=0.05 / 10**9)
+    first = req(0.0, 10**9, 31)
+    small31 = [req(0.002 + 0.001 * i, 10**5 * (i + 1), 31) for i in range(4)]
+    small63 = [req(0.003 + 0.001 * i, 10**5, 63) for i in range(3)]
+    huge31 = req(0.004, 10**9, 31)
+    reqs = [first] + small31 + small63 + [huge31]
+    info = sv.serve_async(c, reqs, budget_bytes=1 << 50, keep_digest=False, policy="sjf", depth=1, batch=True)
+    assert [k for k, _ in c.batches] == [31, 63] or [k for k, _ in c.batches] == [63, 31]
+    b31 = dict(c.batches)[31]
+    assert sorted(b31) == sorted(r.n_bases for r in small31)  # the huge one is not in it
+    assert sorted(dict(c.batches)[63]) == [10**5] * 3
+    assert info["batches"] == 4  # first, two batches, huge
+    assert all(r.done >= r.arrival and r.n_distinct == r.n_bases for r in reqs)
+    assert huge31.done > max(r.done for r in small31 + small63)
+
+
+def test_async_batching_respects_budget_and_max_batch():
+    c = FakeAsyncCounter(seconds_per_base=0.05 / 10**9)
+    blocker = req(0.0, 10**9, 21)
+    many = [req(0.001, 10**5, 21) for _ in range(10)]
+    budget = sv.footprint(blocker) + 3 * sv.footprint(many[0])
+    sv.serve_async(c, [blocker] + many, budget_bytes=budget, keep_digest=False, policy="fifo", depth=1, batch=True,
+                   max_batch=6)
+    sizes = [len(b) for _, b in c.batches]
+    assert max(sizes) <= 6 and sum(sizes) + (len(c.submitted) - sum(sizes)) == 11
+    assert all(r.done >= r.arrival for r in many)
