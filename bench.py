@@ -520,6 +520,76 @@ def run_serve(args):
     counter.close()
 
 
+WORKLOAD_DESC["ablation_aggregation"] = (
+    "aggregation ablation (the GPU analogue of adding the paper's L2 and L3 layers one at a time) on "
+    "uniform_1mbp_100bp_10x_k31 and repeats_100mbp_150bp_30x_k31: L0-L1 = pass B writes every key on its own "
+    "through global atomic cursors and the count kernel adds every key on its own; L0-L2 = shared-memory "
+    "buckets in pass B; L0-L3 = and the warp merge of equal keys in the count kernel (the default)")
+ABLATION_VARIANTS = (("L0-L1", True, True), ("L0-L2", False, True), ("L0-L3", False, False))
+
+
+def run_ablation(args):
+    """Each aggregation variant timed like the plain counter (CUDA events on the plan's stream,
+    inputs in HBM), on configs 1 and 2; every variant's result digest must equal the default's."""
+    import torch
+    import synth
+    from paper_2505_04431_gb300 import KmerCounter
+    from paper_2505_04431_gb300 import build as kcbuild
+    from paper_2505_04431_gb300 import serve as sv
+
+    torch.cuda.set_device(0)
+    kcbuild.build()
+    out = {}
+    launches = 0
+    for wl in ("uniform_1mbp_100bp_10x_k31", "repeats_100mbp_150bp_30x_k31"):
+        reads, offsets, k = synth.workload(wl, args.scale)
+        r_dev = torch.from_numpy(reads).cuda()
+        o_dev = torch.from_numpy(offsets.view(np.int64)).cuda()
+        torch.cuda.synchronize()
+        res_wl, ref = {}, None
+        for name, no_buckets, no_merge in reversed(ABLATION_VARIANTS):  # the default first: the reference
+            stream = torch.cuda.Stream()
+            c = KmerCounter(stream=stream, profile=True, no_smem_buckets=no_buckets, no_warp_merge=no_merge)
+            res = c.count(r_dev, o_dev, k, True)
+            dig = sv._digest(res)
+            res.free()
+            if ref is None:
+                ref = dig
+            elif dig != ref:
+                raise RuntimeError(f"{wl} {name}: result differs from the default")
+            for _ in range(args.warmup):
+                c.count(r_dev, o_dev, k, True).free()
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ktimes = {}
+            ev0.record(stream)
+            for _ in range(args.steps):
+                c.count(r_dev, o_dev, k, True).free()
+                launches += c.stats()["kernel_launches"]
+                for kn, ms in c.kernel_times():
+                    ktimes.setdefault(kn, []).append(ms)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / args.steps
+            kms = {kn: sum(v) / len(v) for kn, v in ktimes.items()}
+            res_wl[name] = {"value": dig[1] / (ms / 1e3) / 1e9, "ms_per_step": ms,
+                            "pass_b_ms": kms.get("k_scatter", 0.0) + kms.get("k_direct_cursors", 0.0),
+                            "count_ms": kms.get("k_count_emit", 0.0)}
+            c.close()
+        base = res_wl["L0-L1"]["ms_per_step"]
+        for name in res_wl:
+            res_wl[name]["speedup_over_L0_L1"] = base / res_wl[name]["ms_per_step"]
+        out[wl] = res_wl
+    head = out["repeats_100mbp_150bp_30x_k31"]["L0-L3"]
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "genome_scale": args.scale,
+                       "parallelism": "1 GPU", "timing": "CUDA events on the plan's stream, per-kernel events"},
+            "ablation": out, "results_identical": True, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -539,6 +609,8 @@ def main():
         run_batch(args)
     elif args.workload.startswith("serve_"):
         run_serve(args)
+    elif args.workload == "ablation_aggregation":
+        run_ablation(args)
     else:
         run_ours(args)
 

@@ -783,7 +783,9 @@ __device__ __forceinline__ uint64_t key_hash(u128 key) {
 // KEEP_C: each window's coarse partition is kept in shared memory (taken in phase 1,
 // carried to the staging and the write-out) instead of being recomputed from the key
 // twice; used when two blocks per SM still fit.
-template <int KW, int NT, bool KEEP_C>
+// DIRECT (the aggregation ablation without per-block buckets): every valid window takes its
+// slot with a global atomic on its partition's cursor and is written on its own.
+template <int KW, int NT, bool KEEP_C, bool DIRECT = false>
 __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, uint32_t bid) {
   typedef typename KeyT<KW>::T K;
   constexpr int WPT = KW == 1 ? 32 : 16;    // windows per thread
@@ -862,8 +864,14 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
         const uint64_t hh = key_hash(keys[i]);
         const bool v = (valid >> i) & 1u;
         if (v) {
-          if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
-          rr[i >> 1] |= atomicAdd(&hist[PAD(c)], 1u) << (16 * (i & 1));
+          if constexpr (DIRECT) {
+            const unsigned long long pos = atomicAdd(&b.fcur[c], 1ull);
+            if (pos < s.cap) store_key(b.kbuf, pos, keys[i]);
+            else atomicOr(&b.meta->status, ST_INTERNAL);
+          } else {
+            if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
+            rr[i >> 1] |= atomicAdd(&hist[PAD(c)], 1u) << (16 * (i & 1));
+          }
         }
         if (v && (hh >> (64 - kHllSampleLog2)) == 0) {
           const uint32_t reg = (uint32_t)(hh >> (64 - kHllSampleLog2 - kHllLog2)) & (kHllRegs - 1);
@@ -872,6 +880,7 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
         }
       }
     }
+    if constexpr (DIRECT) continue;
     __syncthreads();
     for (int c = t; c < P1; c += NT) soff[PAD(c)] = hist[PAD(c)];
     __syncthreads();
@@ -916,6 +925,16 @@ template <int KW, int NT, bool KEEP_C>
 __global__ void __launch_bounds__(NT, 2) k_scatter(Shape s, Buffers b) {
   scatter_body<KW, NT, KEEP_C>(s, b, blockIdx.x);
 }
+// Aggregation ablation: the partition cursors start at the partition starts, and pass B
+// writes every key on its own through them.
+__global__ void k_direct_cursors(const uint64_t* cstart, unsigned long long* cur, int P1) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P1; c += gridDim.x * blockDim.x) cur[c] = cstart[c];
+}
+template <int KW>
+__global__ void __launch_bounds__(256, 2) k_scatter_direct(Shape s, Buffers b) {
+  scatter_body<KW, 256, false, true>(s, b, blockIdx.x);
+}
+
 template <int KW, int NT, bool KEEP_C>
 __global__ void __launch_bounds__(NT, 2) k_scatter_batch(BatchTab t) {
   KC_BATCH_PROLOGUE(t);
@@ -1419,7 +1438,9 @@ __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
 // Count the keys in[0, n) (only those in [lo, hi] when `ranged`).  The all-ones key is
 // counted apart in *special (it marks empty slots); it exists only when the k-mer fills
 // the key word (full_width).  Sets *ovf if a key found no slot.
-template <int KW>
+// With MERGE off (the aggregation ablation without heavy-hitter merging) every key is
+// added on its own.
+template <int KW, bool MERGE = true>
 __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
                           typename KeyT<KW>::T hi, int bT, bool full_width, uint32_t* n_new, uint32_t* ovf,
                           uint32_t* special, uint32_t* status) {
@@ -1446,7 +1467,7 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
       // a warp whose active keys all equal lane 0's key (a heavy hitter) adds them at once;
       // lane 0's own key counts only if it is active, so any inactive lane 0 is harmless
       const K k0 = shfl_key(key, 0);
-      if (__all_sync(0xffffffffu, !act || key == k0)) {
+      if (MERGE && __all_sync(0xffffffffu, !act || key == k0)) {
         const unsigned am = __ballot_sync(0xffffffffu, act);
         if (am && lane == __ffs(am) - 1) {
           const uint32_t inc = __popc(am);
@@ -1722,7 +1743,7 @@ __device__ __forceinline__ void emit_slots(Table<KW> tb, const uint16_t* idx, ui
 
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
-template <int KW>
+template <int KW, bool MERGE = true>
 __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
@@ -1801,7 +1822,8 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
     table_clear<KW>(tb, 1u << bT);
     block_sync();
     phase(0);
-    count_all<KW>(tb, in, n, false, K(0), K(0), bT, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+    count_all<KW, MERGE>(tb, in, n, false, K(0), K(0), bT, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s,
+                         &b.meta->status);
     block_sync();
     phase(1);
     const uint32_t dn = nnew_s;
@@ -1919,7 +1941,8 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
         }
         table_clear<KW>(tb, cap_slots);
         block_sync();
-        count_all<KW>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s, &b.meta->status);
+        count_all<KW, MERGE>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, &nnew_s, &ovf_s, &special_s,
+                             &b.meta->status);
         block_sync();
         const uint32_t dn2 = nnew_s;
         const K width = hi - lo;
@@ -1993,9 +2016,9 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
     }
   }
 }
-template <int KW>
+template <int KW, bool MERGE = true>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffers b) {
-  count_emit_body<KW>(s, b);
+  count_emit_body<KW, MERGE>(s, b);
 }
 template <int KW>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit_batch(BatchTab t) {
@@ -2168,6 +2191,8 @@ int configure_kernels(int device) {
   KC_SET((k_scatter<2, 256, false>));
   KC_SET((k_scatter<1, 256, true>));
   KC_SET((k_scatter<2, 256, true>));
+  KC_SET(k_scatter_direct<1>);
+  KC_SET(k_scatter_direct<2>);
   KC_SET(k_fine_plan);
   KC_SET(k_fine_hist<1>);
   KC_SET(k_fine_hist<2>);
@@ -2175,6 +2200,8 @@ int configure_kernels(int device) {
   KC_SET(k_fine_scatter<2>);
   KC_SET(k_count_emit<1>);
   KC_SET(k_count_emit<2>);
+  KC_SET((k_count_emit<1, false>));
+  KC_SET((k_count_emit<2, false>));
   KC_SET(k_bucket_scan);
   KC_SET(k_pack_count_batch<1>);
   KC_SET(k_pack_count_batch<2>);
@@ -2247,7 +2274,13 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<2, 256, true>, 256, smK);
     const bool keep_c = per_sm >= 2;
     const unsigned gt = (unsigned)s.n_tiles;
-    if (s.kw == 1) {
+    if (s.ablate & kAblateNoSmemBuckets) {
+      k_direct_cursors<<<(P1 + 255) / 256, 256, 0, st>>>(b.cstart, b.fcur, P1);
+      ++launches;
+      KC_STEP("k_direct_cursors");
+      if (s.kw == 1) k_scatter_direct<1><<<gt, 256, smB, st>>>(s, b);
+      else k_scatter_direct<2><<<gt, 256, smB, st>>>(s, b);
+    } else if (s.kw == 1) {
       if (keep_c) k_scatter<1, 256, true><<<gt, 256, smK, st>>>(s, b);
       else k_scatter<1, 256, false><<<gt, 256, smB, st>>>(s, b);
     } else {
@@ -2274,8 +2307,14 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   ++launches;
   KC_STEP("k_fine_scatter");
   const size_t smC = count_kernel_smem(s.kw, s.bT_max, s.tail);
-  if (s.kw == 1) k_count_emit<1><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
-  else k_count_emit<2><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+  if (s.ablate & kAblateNoWarpMerge) {
+    if (s.kw == 1) k_count_emit<1, false><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+    else k_count_emit<2, false><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+  } else if (s.kw == 1) {
+    k_count_emit<1><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+  } else {
+    k_count_emit<2><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+  }
   ++launches;
   KC_STEP("k_count_emit");
   k_scan_distinct<<<1, 1024, 0, st>>>(s, b);
