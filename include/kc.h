@@ -76,15 +76,16 @@ typedef struct {
 /* Testing: kc_count_batch's scratch arena (counts that share batched launches) is limited
  * to 32 MiB, so that small batches form several groups and larger counts run alone. */
 #define KC_PLAN_BATCH_ARENA_SMALL 4u
-/* Aggregation ablation (the GPU analogue of the paper's experiment that adds its L2 and L3
- * aggregation layers one at a time, Section VI): the result is unchanged, only the work
- * differs.  NO_SMEM_BUCKETS: pass B writes every key on its own through a global atomic
- * cursor per partition, instead of grouping each tile's keys by partition in shared memory
- * and writing runs (the L2 per-destination buffers).  NO_WARP_MERGE: the count kernel adds
- * every key on its own, instead of adding a warp's equal keys at once (the L3 heavy-hitter
- * merge).  kc_count only; kc_count_batch ignores NO_SMEM_BUCKETS. */
+/* Aggregation variants (the GPU analogue of the paper's experiment that adds its L2 and L3
+ * aggregation layers one at a time, Section VI); the result is unchanged, only the work
+ * differs.  ABLATE_NO_SMEM_BUCKETS: pass B writes every key on its own through a global
+ * atomic cursor per partition, instead of grouping each tile's keys by partition in shared
+ * memory and writing runs (the L2 per-destination buffers).  WARP_MERGE: the count kernel
+ * adds a warp's equal keys with one atomic (the L3 heavy-hitter merge); off by default,
+ * because on GB300 the shared-memory atomics absorb equal keys faster than the merge's warp
+ * vote costs, even when every key is the same.  kc_count only. */
 #define KC_PLAN_ABLATE_NO_SMEM_BUCKETS 8u
-#define KC_PLAN_ABLATE_NO_WARP_MERGE 16u
+#define KC_PLAN_WARP_MERGE 16u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */

@@ -91,7 +91,7 @@ struct kc_plan_s {
   bool profile = false;
   bool defer_all = false;
   bool small_arena = false;
-  int ablate = 0;
+  int aggr = 0;
   static constexpr int kMaxMarks = 32;
   cudaEvent_t ev[kMaxMarks + 1] = {};
   const char* ev_name[kMaxMarks] = {};
@@ -234,7 +234,7 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   s.smem_budget = p->smem_optin;
   s.profile = p->profile ? 1 : 0;
   s.defer_all = p->defer_all ? 1 : 0;
-  s.ablate = p->ablate;
+  s.aggr = p->aggr;
   const uint64_t P1 = (uint64_t)j.P1, nf = j.nf_max;
   Layout lay;
   j.o_reads = lay.add(j.copy_reads ? L + 16 : 0);
@@ -620,8 +620,8 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->profile = (opts->flags & KC_PLAN_PROFILE) != 0;
   p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
   p->small_arena = (opts->flags & KC_PLAN_BATCH_ARENA_SMALL) != 0;
-  p->ablate = ((opts->flags & KC_PLAN_ABLATE_NO_SMEM_BUCKETS) ? kc::kAblateNoSmemBuckets : 0) |
-              ((opts->flags & KC_PLAN_ABLATE_NO_WARP_MERGE) ? kc::kAblateNoWarpMerge : 0);
+  p->aggr = ((opts->flags & KC_PLAN_ABLATE_NO_SMEM_BUCKETS) ? kc::kAggrNoSmemBuckets : 0) |
+            ((opts->flags & KC_PLAN_WARP_MERGE) ? kc::kAggrWarpMerge : 0);
   if (p->profile) {
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) {
       if ((e = cudaEventCreate(&p->ev[i])) != cudaSuccess) {

@@ -74,10 +74,10 @@ struct Shape {
   uint64_t smem_budget; // opt-in shared memory per block
   int profile;          // nonzero: k_count_emit accumulates per-phase cycle counts
   int defer_all;        // nonzero (testing): every fine partition takes the deferred write-out
-  int ablate;           // aggregation ablation: kAblate* bits (single-count path only)
+  int aggr;             // aggregation variants: kAggr* bits (single-count path only)
 };
-constexpr int kAblateNoSmemBuckets = 1;  // pass B writes every key on its own (global atomic cursor)
-constexpr int kAblateNoWarpMerge = 2;    // the count kernel adds every key on its own
+constexpr int kAggrNoSmemBuckets = 1;  // pass B writes every key on its own (global atomic cursor)
+constexpr int kAggrWarpMerge = 2;      // the count kernel adds a warp's equal keys with one atomic
 
 struct Buffers {
   const uint8_t* reads;

@@ -1438,9 +1438,11 @@ __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
 // Count the keys in[0, n) (only those in [lo, hi] when `ranged`).  The all-ones key is
 // counted apart in *special (it marks empty slots); it exists only when the k-mer fills
 // the key word (full_width).  Sets *ovf if a key found no slot.
-// With MERGE off (the aggregation ablation without heavy-hitter merging) every key is
-// added on its own.
-template <int KW, bool MERGE = true>
+// With MERGE, a warp whose active keys are all equal adds them with one atomic (the
+// heavy-hitter merge of the paper's L3 layer); without it (the default) every key is added
+// on its own: on GB300 the shared-memory atomics absorb equal keys faster than the merge's
+// warp vote costs, even for a single key.
+template <int KW, bool MERGE = false>
 __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
                           typename KeyT<KW>::T hi, int bT, bool full_width, uint32_t* n_new, uint32_t* ovf,
                           uint32_t* special, uint32_t* status) {
@@ -1743,7 +1745,7 @@ __device__ __forceinline__ void emit_slots(Table<KW> tb, const uint16_t* idx, ui
 
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
-template <int KW, bool MERGE = true>
+template <int KW, bool MERGE = false>
 __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
@@ -2016,7 +2018,7 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
     }
   }
 }
-template <int KW, bool MERGE = true>
+template <int KW, bool MERGE = false>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count_emit(Shape s, Buffers b) {
   count_emit_body<KW, MERGE>(s, b);
 }
@@ -2200,8 +2202,8 @@ int configure_kernels(int device) {
   KC_SET(k_fine_scatter<2>);
   KC_SET(k_count_emit<1>);
   KC_SET(k_count_emit<2>);
-  KC_SET((k_count_emit<1, false>));
-  KC_SET((k_count_emit<2, false>));
+  KC_SET((k_count_emit<1, true>));
+  KC_SET((k_count_emit<2, true>));
   KC_SET(k_bucket_scan);
   KC_SET(k_pack_count_batch<1>);
   KC_SET(k_pack_count_batch<2>);
@@ -2274,7 +2276,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scatter<2, 256, true>, 256, smK);
     const bool keep_c = per_sm >= 2;
     const unsigned gt = (unsigned)s.n_tiles;
-    if (s.ablate & kAblateNoSmemBuckets) {
+    if (s.aggr & kAggrNoSmemBuckets) {
       k_direct_cursors<<<(P1 + 255) / 256, 256, 0, st>>>(b.cstart, b.fcur, P1);
       ++launches;
       KC_STEP("k_direct_cursors");
@@ -2307,9 +2309,9 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   ++launches;
   KC_STEP("k_fine_scatter");
   const size_t smC = count_kernel_smem(s.kw, s.bT_max, s.tail);
-  if (s.ablate & kAblateNoWarpMerge) {
-    if (s.kw == 1) k_count_emit<1, false><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
-    else k_count_emit<2, false><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+  if (s.aggr & kAggrWarpMerge) {
+    if (s.kw == 1) k_count_emit<1, true><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
+    else k_count_emit<2, true><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
   } else if (s.kw == 1) {
     k_count_emit<1><<<(unsigned)n_sms, kCountThreads, smC, st>>>(s, b);
   } else {

@@ -370,17 +370,17 @@ def test_golden_aatgg_repeat(counter):
             res.free()
 
 
-@pytest.mark.parametrize("no_buckets,no_merge", [(True, True), (False, True), (True, False)])
-def test_aggregation_ablation_keeps_the_result(torch_cuda, no_buckets, no_merge):
-    """The aggregation-ablation plans (pass B without shared-memory buckets, count kernel
-    without the warp merge of equal keys) compute the same histogram."""
+@pytest.mark.parametrize("no_buckets,merge", [(True, False), (False, True), (True, True)])
+def test_aggregation_variants_keep_the_result(torch_cuda, no_buckets, merge):
+    """The aggregation variants (pass B without shared-memory buckets, count kernel with the
+    warp merge of equal keys) compute the same histogram."""
     from paper_2505_04431_gb300 import KmerCounter
-    c = KmerCounter(no_smem_buckets=no_buckets, no_warp_merge=no_merge)
+    c = KmerCounter(no_smem_buckets=no_buckets, warp_merge=merge)
     try:
         cases = [synth.generate(synth.REPEAT_SHORT, 1002, 0.001)[:2],
                  (np.frombuffer(b"ACGTTGCA" * 4000, dtype=np.uint8).copy(), np.array([0, 32000], np.uint64))]
         for reads, offsets in cases:
             for k, canonical in ((31, True), (21, False), (63, True)):
-                assert_parity(c, reads, offsets, k, canonical, f"ablation {no_buckets} {no_merge} k={k}")
+                assert_parity(c, reads, offsets, k, canonical, f"variant {no_buckets} {merge} k={k}")
     finally:
         c.close()
