@@ -126,7 +126,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   s.canonical = canonical ? 1 : 0;
   s.kw = k <= 32 ? 1 : 2;
   {
-    const int want = clog2(L / (6u << 20) + 1);  // the same rule as kc_count
+    const int want = clog2(L / kc::coarse_bases(s.kw) + 1);  // the same rule as kc_count
     s.b1 = want < 11 ? want : 11;
   }
   const int P1 = 1 << s.b1;
