@@ -110,7 +110,8 @@ kc_status kc_plan(const kc_plan_opts *opts, kc_plan_t *out);
  *   k        1..64.   canonical  0: forward keys; nonzero: canonical keys.
  * On KC_OK, *out holds device buffers owned by the library until kc_free.
  * The call is synchronous with respect to the plan's stream (it returns after
- * the result is complete).
+ * the result is complete).  The order of the offsets is checked on the device (host
+ * offsets too), so that a long offsets array costs no host-side pass.
  * Errors: KC_EINVAL (k out of range, NULL pointers, offsets[0] != 0, offsets not
  * non-decreasing), KC_ENOMEM, KC_ECUDA, KC_EOVERFLOW (a count above 2^32 - 1),
  * KC_ETIMEOUT (device wait limit hit).  On any error *out is zeroed. */
