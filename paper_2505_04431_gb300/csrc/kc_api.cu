@@ -1110,14 +1110,15 @@ kc_status kc_submit_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const*
 }
 
 static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done, bool block) {
+  const std::string who = block ? "kc_job_wait" : "kc_job_poll";
   g_err.clear();
-  if (!p || !out || !done) return fail(KC_EINVAL, "kc_job_poll: NULL argument");
+  if (!p || !out || !done) return fail(KC_EINVAL, who + ": NULL argument");
   *done = 0;
   memset(out, 0, sizeof(*out));
   ScopedBusy busy(p);
-  if (!busy.ok) return fail(KC_EBUSY, "kc_job_poll: plan in use by another call");
+  if (!busy.ok) return fail(KC_EBUSY, who + ": plan in use by another call");
   auto it = p->jobs.find(id);
-  if (it == p->jobs.end()) return fail(KC_EINVAL, "kc_job_poll: no such job");
+  if (it == p->jobs.end()) return fail(KC_EINVAL, who + ": no such job");
   AsyncJob* a = it->second;
   cudaSetDevice(p->device);
   const cudaError_t q = block ? cudaEventSynchronize(a->ev) : cudaEventQuery(a->ev);
@@ -1125,16 +1126,15 @@ static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done
   *done = 1;
   if (q != cudaSuccess) {
     retire(p, id, a, true);
-    return cuda_fail(q, "kc_job_poll");
+    return cuda_fail(q, who.c_str());
   }
   const kc::Meta m = p->pinned[a->slot];
   std::string msg;
-  const kc_status stc = job_status(a->j, m, "kc_job_poll", &msg);
+  const kc_status stc = job_status(a->j, m, who.c_str(), &msg);
   if (stc != KC_OK) {
     retire(p, id, a, true);
     return fail(stc, msg);
   }
-  memset(out, 0, sizeof(*out));
   fill_result(a->j, m, out);
   out->_owner = a->owner;  // the result keeps the job's reference on the group's buffers
   record_stats(p, a->j, m);
