@@ -14,23 +14,30 @@
 //                           Section IV-C / Algorithm 4 (AddToL2Buffer), which exist to
 //                           turn many small sends into few large ones.
 // Phase 2 (Algorithm 3 after the barrier: Sort + Accumulate; Section V "Phase 2"):
-//   k_fine_hist, k_fine_scan, k_fine_scatter   split every owner partition into fine
-//                           partitions small enough for one shared-memory table.
-//   k_count_emit            per fine partition: insert every key into an
-//                           order-preserving open-addressing table in shared memory
-//                           (CAS claims the slot, a 32-bit atomic add counts; a warp
-//                           whose 32 keys are equal adds once, the warp-level form of
-//                           the heavy-hitter pre-aggregation of Section IV-D), sort the
-//                           few keys displaced by collisions, and emit the sorted
-//                           (key, count) run at the offset found by a decoupled
-//                           look-back over the fine partitions.
+//   k_fine_plan, k_fine_hist, k_fine_scan, k_fine_scatter   split every owner partition
+//                           into fine partitions small enough for one shared-memory table
+//                           (sized from a HyperLogLog estimate of the distinct keys).
+//   k_count_emit            persistent; per fine partition: count every key in a hashed
+//                           open-addressing table in shared memory (CAS claims a slot, a
+//                           32-bit atomic add counts), order the occupied slots by a
+//                           bucketed counting sort over the partition's key range, and
+//                           write the sorted (key, count) run at the offset found by a
+//                           decoupled look-back over the fine partitions, or in its own
+//                           input region when that offset is not known in time.
+//   k_scan_distinct, k_compact   output offsets of all runs; the runs written in place
+//                           move to their offsets.
+// Variants: every kernel body also runs as a batched kernel (one launch for a group of
+// counts, each thread block working for one count found through a block table); pass B
+// without the shared-memory staging (DIRECT) and the count kernel with a warp-level merge
+// of equal keys (the heavy-hitter pre-aggregation of Section IV-D; slower on GB300, so off
+// by default) exist for the aggregation experiment of Section VI.
 //
 // Owner partitions are key ranges (not hashes) so that the per-partition outputs
-// concatenate into one ascending array.  A monotone map u(key) from the top 64 key
-// bits flattens the distribution of canonical keys (min of two near-independent
-// uniforms has density 2(1-x); u = 1 - (1-x)^2 is its distribution function), and
-// coarse partition, fine partition and table home slot are consecutive bit fields
-// of u, so every one of them is non-decreasing in the key.
+// concatenate into one ascending array.  A monotone map u(key) of the top 32 key bits
+// flattens the distribution of canonical keys (the min of two near-independent uniforms
+// has density 2(1-x); u = 1 - (1-x)^2 is its distribution function); the coarse partition
+// is the top bits of u and the fine partitions split each coarse range of u into equal
+// parts, so both are non-decreasing in the key.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
