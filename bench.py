@@ -58,10 +58,17 @@ def measured_peaks():
 
 
 def source_hash():
+    """Hash of the kernel source's code (comments and blank lines left out), so that a
+    comment edit keeps the DRAM figures captured on that code."""
+    import re
     h = hashlib.sha256()
     for f in ("kc_kernels.cu", "kc_internal.h"):
-        with open(os.path.join(ROOT, "paper_2505_04431_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2505_04431_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
