@@ -208,11 +208,11 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   int b1;
   if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
   else {
-    // coarse partitions of at most about 12 Mi windows (64-bit keys) or 6 Mi (128-bit keys,
-    // whose tables hold half as many): few enough partitions that pass B's per-partition
-    // runs stay long, small enough that a partition of distinct keys splits into at most
-    // ~1400 fine partitions (measured on GB300: 256 coarse partitions for 3 G bases of
-    // 64-bit keys beat 512 and 128)
+    // coarse partitions of at most about 12 Mi windows (64-bit keys) or 6 Mi (128-bit keys):
+    // few enough partitions that pass B's per-partition runs stay long, small enough that a
+    // partition of distinct keys splits into at most ~2800 (64-bit) or ~1400 (128-bit) fine
+    // partitions of one table each, within kMaxFine (measured on GB300: 256 coarse
+    // partitions for 3 G bases of 64-bit keys beat 512 and 128)
     const int want = ceil_log2_u64(L / kc::coarse_bases(s.kw) + 1);
     b1 = want < 11 ? want : 11;
   }

@@ -22,7 +22,7 @@ constexpr int kTileWords = 8192;               // one phase-1 tile = 262144 base
 constexpr uint64_t kTileBases = (uint64_t)kTileWords * kWordBases;
 constexpr int kPackThreads = 512;              // pass A: one code word per thread per sub-step
 constexpr int kMaxCoarseLog2 = 12;             // at most 4096 coarse partitions
-constexpr int kMaxFine = 2048;                 // at most this many fine partitions per coarse one
+constexpr int kMaxFine = 4096;                 // at most this many fine partitions per coarse one
 // bases per coarse partition aimed at when the plan sets no partition count
 constexpr uint64_t coarse_bases(int kw) { return kw == 1 ? (12ull << 20) : (6ull << 20); }
 constexpr int kCountThreads = 1024;            // phase-2 count/emit CTA
