@@ -122,6 +122,8 @@ def test_uncollected_jobs_released_on_close(torch_cuda):
 
 
 def make_requests(torch, n=40, seed=7):
+    """n requests over 6 read sets: the first half arrive at once (so that requests surely
+    wait together), the rest at Poisson times."""
     from paper_2505_04431_gb300 import serve as sv
     pool = []
     for i in range(6):
@@ -129,8 +131,10 @@ def make_requests(torch, n=40, seed=7):
         pool.append((torch.from_numpy(r).cuda(), torch.from_numpy(o.view(np.int64)).cuda(), int(o[-1])))
     torch.cuda.synchronize()
     rng = np.random.RandomState(seed)
+    arrivals = np.cumsum(rng.exponential(0.002, n))
+    arrivals[: n // 2] = 0.0
     return [sv.Request(float(t), *pool[p], int(k)) for t, p, k in
-            zip(np.cumsum(rng.exponential(0.002, n)), rng.randint(0, 6, n), rng.choice([21, 31, 63], n))]
+            zip(arrivals, rng.randint(0, 6, n), rng.choice([21, 31, 63], n))]
 
 
 def digests_alone(counter, reqs):
