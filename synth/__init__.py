@@ -42,10 +42,11 @@ class _Out(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile synth.c into libsynth.so beside it (plain gcc, portable flags)."""
+    """Compile synth.c into libsynth.so beside it (plain gcc, portable flags; no fused
+    multiply-add contraction, so that x86-64 and Arm builds draw the same reads)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
