@@ -386,7 +386,7 @@ def run_batch(args):
             res = counter.count(r, o, 31, True)
             v += res.n_valid_windows
             if digests is not None:
-                digests.append(sv._digest(res))
+                digests.append(sv.result_digest(res))
             res.free()
         return v
 
@@ -394,7 +394,7 @@ def run_batch(args):
         out = counter.count_batch(samples, 31, True)
         v = sum(res.n_valid_windows for res in out)
         if digests is not None:
-            digests.extend(sv._digest(res) for res in out)
+            digests.extend(sv.result_digest(res) for res in out)
         for res in out:
             res.free()
         return v
@@ -479,7 +479,7 @@ def run_serve(args):
     ref = {}
     for p_, k_ in sorted(set(zip(picks.tolist(), ks.tolist()))):
         res = counter.count(pool[p_][0], pool[p_][1], k_)
-        ref[(p_, k_)] = sv._digest(res)
+        ref[(p_, k_)] = sv.result_digest(res)
         res.free()
     # timed: latency to the completion of each count (results stay on the device)
     runs = {}
@@ -572,7 +572,7 @@ def run_ablation(args):
             stream = torch.cuda.Stream()
             c = KmerCounter(stream=stream, profile=True, no_smem_buckets=no_buckets, warp_merge=merge)
             res = c.count(r_dev, o_dev, k, True)
-            dig = sv._digest(res)
+            dig = sv.result_digest(res)
             res.free()
             if ref is None:
                 ref = dig

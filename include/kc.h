@@ -57,7 +57,8 @@ typedef struct {
   kc_free_fn free_;           /* NULL: cudaFreeAsync on `stream` */
   void *alloc_ctx;            /* passed back to alloc / free_ */
   uint64_t max_device_bytes;  /* 0: no limit; else kc_count fails with KC_ENOMEM above it */
-  uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 4096); 0: chosen from input size */
+  uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 2048; at most 1024 are used for
+                                 k > 32); 0: chosen from input size */
   uint32_t block_size_hint;   /* reserved (0) */
   float table_load;           /* distinct keys aimed at per fine partition, as a fraction of the
                                  count table's slots (the fine split is sized by it); 0: 0.55 */
@@ -69,9 +70,9 @@ typedef struct {
 /* kc_plan_opts.flags: record a CUDA event on the plan's stream after every kernel
  * launch of kc_count, so kc_last_kernel_times can report each kernel's device time. */
 #define KC_PLAN_PROFILE 1u
-/* Testing: every fine partition writes its run to its own input region and the final
- * compaction pass moves it (the path taken when a partition's output offset is not yet
- * known when it is ready to write). */
+/* Testing: every fine partition leaves its sorted run in its thread block's stage and
+ * writes it out later (the path taken when a partition's output offset is not yet known
+ * when it is ready to write). */
 #define KC_PLAN_DEFER_ALL 2u
 /* Testing: kc_count_batch's scratch arena (counts that share batched launches) is limited
  * to 32 MiB, so that small batches form several groups and larger counts run alone. */
@@ -86,6 +87,10 @@ typedef struct {
  * vote costs, even when every key is the same.  kc_count only. */
 #define KC_PLAN_ABLATE_NO_SMEM_BUCKETS 8u
 #define KC_PLAN_WARP_MERGE 16u
+/* Testing: the first fine partition never publishes its output offset and the device-side
+ * wait for it is cut to a few iterations, so that the later partitions' bounded waits run
+ * out: kc_count then returns KC_ETIMEOUT (no GPU fault, no hang). */
+#define KC_PLAN_TEST_WITHHOLD_PREFIX 32u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */
@@ -175,15 +180,18 @@ kc_status kc_last_kernel_times(kc_plan_t plan, uint32_t max, const char **names,
  *   n_distinct, n_valid_windows   host pointers, written on success.
  *   stream          cudaStream_t (NULL = legacy default); the call returns after the
  *                   result is complete on it.
+ * Alignment: offsets 8 bytes, out_counts 4 bytes, out_keys 8 bytes (16 bytes for k > 32);
+ * a misaligned buffer is refused on the host before anything is launched.
  * The first call on a device (with that device current) looks up the scratch array's
  * device address and sets kernel attributes; make that first call before any stream
- * capture.  All calls share the one array, and each call clears what it needs: calls
+ * capture.  Every call reads the offsets and its status record back, so it synchronises
+ * its stream.  All calls share the one array, and each call clears what it needs: calls
  * that overlap on the GPU (other streams, other host threads) race and must not be made.
  * Errors: KC_EINVAL (sizes beyond the maximum, host or misaligned buffers, small
  * out_capacity, bad k or offsets), KC_ECUDA, KC_EOVERFLOW, KC_ETIMEOUT; kc_last_error()
  * gives the message. */
 #define KC_NOALLOC_MAX_BASES (1u << 20)
-#define KC_NOALLOC_SCRATCH_BYTES (48u << 20)
+#define KC_NOALLOC_SCRATCH_BYTES (64u << 20)
 kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, int k, int canonical,
                            uint64_t *out_keys, uint32_t *out_counts, uint64_t out_capacity, uint64_t *n_distinct,
                            uint64_t *n_valid_windows, void *stream);

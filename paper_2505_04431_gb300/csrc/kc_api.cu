@@ -46,6 +46,137 @@ constexpr size_t kBatchArenaBytes = 16ull << 30;
 
 namespace kc {
 void set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
+static int ceil_log2_u64(uint64_t v) { return v <= 1 ? 0 : 64 - __builtin_clzll(v - 1); }
+
+uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int canonical, bool copy_reads,
+                    bool copy_offs, Shape& s, Layout& lay) {
+  s = Shape{};
+  s.L = L;
+  s.n_reads = n_reads;
+  s.n_words = (L + 31) / 32;
+  s.n_tiles = (s.n_words + kTileWords - 1) / kTileWords;
+  s.k = k;
+  s.canonical = canonical ? 1 : 0;
+  s.kw = k <= 32 ? 1 : 2;
+  const int bmax = max_coarse_log2(s.kw);
+  int b1;
+  if (o.p_hint) {
+    b1 = ceil_log2_u64(o.p_hint);
+  } else {
+    // coarse partitions of about 3 Mi bases (64-bit keys) or 1.5 Mi (128-bit keys): a
+    // coarse partition's keys and their split copy stay in L2 while phase 2 works on them
+    b1 = ceil_log2_u64(L / coarse_bases(s.kw) + 1);
+  }
+  s.b1 = b1 < bmax ? b1 : bmax;
+  const uint64_t P1 = 1ull << s.b1;
+  int bT_max = table_log2_max(s.kw, o.smem_optin);
+  if (o.slots_max) {
+    const int bt = 63 - __builtin_clzll((uint64_t)o.slots_max);
+    if (bt < bT_max) bT_max = bt;
+  }
+  s.bT_max = bT_max;
+  const double ft = (double)(1u << bT_max) * o.load;  // distinct keys per fine partition aimed at
+  s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
+  s.cap = L > 0 ? L : 1;
+  // sum over partitions of ceil(n_c / target), target >= fine_target: at most K / ft + P1
+  const uint64_t nf_bound = s.cap / s.fine_target + P1 + 1;
+  const uint64_t nf_lim = P1 * kMaxFine;
+  s.nf_max = nf_bound < nf_lim ? nf_bound : nf_lim;
+  // run starts: (m_c + 1) per chunk, m_c <= kMaxFine, at most K / chunk + P1 chunks
+  s.tcap = ((uint64_t)kMaxFine + 1) * (s.cap / split_chunk(s.kw) + P1);
+  // one stage slot per phase-2 block: a block per 8 Ki bases, at most one per SM
+  const uint64_t want_blocks = (L + 8191) / 8192;
+  const uint64_t sms = o.n_sms > 0 ? (uint64_t)o.n_sms : 1;
+  s.n_stage = (uint32_t)(want_blocks < 1 ? 1 : (want_blocks > sms ? sms : want_blocks));
+  // stage slots per block: a partition whose prefix is late waits in a slot; several slots
+  // let a block go on while a slow partition further back holds the prefixes up (at most
+  // a quarter of the block's expected fine partitions)
+  {
+    const uint64_t per = s.nf_max / s.n_stage / 4;
+    s.n_slots = (uint32_t)(per < 1 ? 1 : (per > (uint64_t)kMaxSlots ? (uint64_t)kMaxSlots : per));
+  }
+  s.stage_bytes = (uint32_t)stage_slot_bytes(s.kw, bT_max);
+  s.spin_limit = o.withhold ? kTestSpinLimit : kLookbackSpinLimit;
+  s.smem_budget = o.smem_optin;
+  s.profile = o.profile;
+  s.defer_all = o.defer_all;
+  s.withhold = o.withhold;
+  s.aggr = o.aggr;
+  const uint64_t nf = s.nf_max;
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o_ = at;
+    at = (at + (bytes ? bytes : 1) + 255) / 256 * 256;
+    return o_;
+  };
+  lay.reads = take(copy_reads ? L + 16 : 0);
+  lay.offs = take(copy_offs ? (n_reads + 1) * 8 : 0);
+  lay.codes = take(s.n_words * 8);
+  lay.inv = take(s.n_words * 4);
+  lay.tf = take(s.n_tiles * 8);
+  lay.hist = take(s.n_tiles * P1 * 4);
+  lay.toff = take(s.n_tiles * P1 * 8);
+  lay.cst = take((P1 + 1) * 8);
+  lay.fb = take((P1 + 1) * 4);
+  lay.fm = take(P1 * 4);
+  lay.hll = take((size_t)kHllRegs * 4);
+  lay.fh = take(nf * 4);
+  lay.flo = take((nf + 1) * 4);
+  lay.look = take(nf * 8);
+  lay.tstart = take((P1 + kStageLag + 1) * 4);
+  lay.tsplit = take((P1 + kStageLag) * 4);
+  lay.tbase = take((P1 + 1) * 8);
+  lay.rstart = take(s.tcap * 2);
+  lay.sdone = take(P1 * 4);
+  lay.stage = take((size_t)s.n_stage * s.n_slots * s.stage_bytes);
+  lay.kbuf = take(s.cap * s.kw * 8);
+  lay.sbuf = take(s.cap * s.kw * 8);
+  lay.meta = take(sizeof(Meta));
+  lay.total = at;
+  return (uint32_t)nf;
+}
+
+Buffers layout_buffers(const Layout& lay, uint8_t* ws) {
+  Buffers b{};
+  b.reads = (const uint8_t*)(ws + lay.reads);
+  b.offsets = (const uint64_t*)(ws + lay.offs);
+  b.codes64 = (uint64_t*)(ws + lay.codes);
+  b.inv32 = (uint32_t*)(ws + lay.inv);
+  b.tile_first = (uint64_t*)(ws + lay.tf);
+  b.hist = (uint32_t*)(ws + lay.hist);
+  b.toff = (uint64_t*)(ws + lay.toff);
+  b.cstart = (uint64_t*)(ws + lay.cst);
+  b.fine_base = (uint32_t*)(ws + lay.fb);
+  b.fine_m = (uint32_t*)(ws + lay.fm);
+  b.hll = (uint32_t*)(ws + lay.hll);
+  b.fhist = (uint32_t*)(ws + lay.fh);
+  b.flo = (uint32_t*)(ws + lay.flo);
+  b.look = (unsigned long long*)(ws + lay.look);
+  b.tstart = (uint32_t*)(ws + lay.tstart);
+  b.tsplit = (uint32_t*)(ws + lay.tsplit);
+  b.tbase = (uint64_t*)(ws + lay.tbase);
+  b.rstart = (uint16_t*)(ws + lay.rstart);
+  b.sdone = (uint32_t*)(ws + lay.sdone);
+  b.stage = ws + lay.stage;
+  b.kbuf = (uint64_t*)(ws + lay.kbuf);
+  b.sbuf = (uint64_t*)(ws + lay.sbuf);
+  b.meta = (Meta*)(ws + lay.meta);
+  return b;
+}
+
+// The arrays the kernels expect zeroed at the start of a count (stream-ordered).
+int clear_scratch(const Shape& s, const Buffers& b, void* stream) {
+  const cudaStream_t st = (cudaStream_t)stream;
+  const size_t P1 = (size_t)1 << s.b1;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(b.meta, 0, sizeof(Meta), st)) != cudaSuccess) return (int)e;
+  if ((e = cudaMemsetAsync(b.fhist, 0, (size_t)s.nf_max * 4, st)) != cudaSuccess) return (int)e;
+  if ((e = cudaMemsetAsync(b.hll, 0, (size_t)kHllRegs * 4, st)) != cudaSuccess) return (int)e;
+  if ((e = cudaMemsetAsync(b.look, 0, (size_t)s.nf_max * 8, st)) != cudaSuccess) return (int)e;
+  if ((e = cudaMemsetAsync(b.cstart, 0, (P1 + 1) * 8, st)) != cudaSuccess) return (int)e;
+  return (int)cudaMemsetAsync(b.sdone, 0, P1 * 4, st);
+}
 }  // namespace kc
 
 struct kc_plan_s {
@@ -90,6 +221,7 @@ struct kc_plan_s {
   // per-kernel timing (KC_PLAN_PROFILE)
   bool profile = false;
   bool defer_all = false;
+  bool withhold = false;
   bool small_arena = false;
   int aggr = 0;
   static constexpr int kMaxMarks = 32;
@@ -127,18 +259,6 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct Layout {
-  size_t off[24];
-  int n = 0;
-  size_t total = 0;
-  size_t add(size_t bytes) {
-    const size_t o = total;
-    total = align_up(total + bytes, 256);
-    off[n++] = o;
-    return o;
-  }
-};
-
 struct ScopedBusy {
   kc_plan_s* p;
   bool ok;
@@ -150,8 +270,6 @@ struct ScopedBusy {
     if (ok) p->busy.store(0);
   }
 };
-
-int ceil_log2_u64(uint64_t v) { return v <= 1 ? 0 : 64 - __builtin_clzll(v - 1); }
 
 void record_mark(void* ctx, const char* name) {
   kc_plan_s* p = (kc_plan_s*)ctx;
@@ -174,18 +292,31 @@ void debug_mark(void* ctx, const char* name) {
 // ---- one count: shape and scratch layout (host only), launch sequence, result
 struct Job {
   kc::Shape s{};
+  kc::Layout lay{};
   int P1 = 1;
   uint32_t nf_max = 0;
   uint64_t L = 0, n_reads = 0;
   bool off_dev = false, copy_reads = false, reads_dev = false;
   const uint8_t* reads = nullptr;
   const uint64_t* offsets = nullptr;
-  size_t o_reads = 0, o_offs = 0, o_codes = 0, o_inv = 0, o_tf = 0, o_hist = 0, o_toff = 0, o_cst = 0, o_fb = 0, o_fl = 0,
-         o_hll = 0, o_fh = 0, o_fo = 0, o_flo = 0, o_fc = 0, o_look = 0, o_kbuf = 0, o_sbuf = 0, o_meta = 0;
   size_t ws_bytes = 0, out_key_bytes = 0, out_cnt_bytes = 0;
   void* okeys = nullptr;
   void* ocnts = nullptr;
 };
+
+kc::ShapeOpts shape_opts(const kc_plan_s* p) {
+  kc::ShapeOpts o;
+  o.p_hint = p->p_hint;
+  o.load = p->load;
+  o.slots_max = p->slots_max;
+  o.smem_optin = p->smem_optin;
+  o.n_sms = p->n_sms;
+  o.profile = p->profile ? 1 : 0;
+  o.defer_all = p->defer_all ? 1 : 0;
+  o.withhold = p->withhold ? 1 : 0;
+  o.aggr = p->aggr;
+  return o;
+}
 
 void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t L,
               bool off_dev, int k, int canonical, Job& j) {
@@ -196,95 +327,18 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   j.off_dev = off_dev;
   j.reads_dev = L > 0 && is_device_ptr(reads);
   j.copy_reads = L > 0 && (!j.reads_dev || ((uintptr_t)reads & 15) != 0);
-  kc::Shape& s = j.s;
-  s = kc::Shape{};
-  s.L = L;
-  s.n_reads = n_reads;
-  s.n_words = (L + 31) / 32;
-  s.n_tiles = (s.n_words + kc::kTileWords - 1) / kc::kTileWords;
-  s.k = k;
-  s.canonical = canonical ? 1 : 0;
-  s.kw = k <= 32 ? 1 : 2;
-  int b1;
-  if (p->p_hint) b1 = ceil_log2_u64(p->p_hint);
-  else {
-    // coarse partitions of at most about 12 Mi windows (64-bit keys) or 6 Mi (128-bit keys):
-    // few enough partitions that pass B's per-partition runs stay long, small enough that a
-    // partition of distinct keys splits into at most ~2800 (64-bit) or ~1400 (128-bit) fine
-    // partitions of one table each, within kMaxFine (measured on GB300: 256 coarse
-    // partitions for 3 G bases of 64-bit keys beat 512 and 128)
-    const int want = ceil_log2_u64(L / kc::coarse_bases(s.kw) + 1);
-    b1 = want < 11 ? want : 11;
-  }
-  s.b1 = b1;
-  j.P1 = 1 << b1;
-  int bT_max = kc::table_log2_max(s.kw, p->smem_optin);
-  if (p->slots_max) {
-    const int bt = 63 - __builtin_clzll((uint64_t)p->slots_max);
-    if (bt < bT_max) bT_max = bt;
-  }
-  s.bT_max = bT_max;
-  s.tail = bT_max >= 10 ? 1024 : (1 << bT_max);
-  const double ft = (double)(1u << bT_max) * p->load;  // distinct keys per fine partition aimed at
-  s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
-  s.cap = L > 0 ? L : 1;
-  // sum over partitions of ceil(n_c / target), target >= fine_target: at most K / ft + P1
-  const uint64_t nf_bound = s.cap / s.fine_target + (uint64_t)j.P1 + 1;
-  const uint64_t nf_lim = (uint64_t)j.P1 * kc::kMaxFine;
-  j.nf_max = (uint32_t)(nf_bound < nf_lim ? nf_bound : nf_lim);
-  s.nf_max = j.nf_max;
-  s.smem_budget = p->smem_optin;
-  s.profile = p->profile ? 1 : 0;
-  s.defer_all = p->defer_all ? 1 : 0;
-  s.aggr = p->aggr;
-  const uint64_t P1 = (uint64_t)j.P1, nf = j.nf_max;
-  Layout lay;
-  j.o_reads = lay.add(j.copy_reads ? L + 16 : 0);
-  j.o_offs = lay.add(off_dev ? 0 : (n_reads + 1) * 8);
-  j.o_codes = lay.add(s.n_words * 8);
-  j.o_inv = lay.add(s.n_words * 4);
-  j.o_tf = lay.add(s.n_tiles * 8);
-  j.o_hist = lay.add(s.n_tiles * P1 * 4);
-  j.o_toff = lay.add(s.n_tiles * P1 * 8);
-  j.o_cst = lay.add((P1 + 1) * 8);
-  j.o_fb = lay.add((P1 + 1) * 4);
-  j.o_fl = lay.add(P1 * 4);
-  j.o_hll = lay.add((size_t)kc::kHllRegs * 4);
-  j.o_fh = lay.add(nf * 4);
-  j.o_fo = lay.add((nf + 1) * 8);
-  j.o_flo = lay.add((nf + 1) * 4);
-  j.o_fc = lay.add(nf * 8);
-  j.o_look = lay.add(nf * 8);
-  j.o_kbuf = lay.add(s.cap * s.kw * 8);
-  j.o_sbuf = lay.add(s.cap * s.kw * 8);
-  j.o_meta = lay.add(sizeof(kc::Meta));
-  j.ws_bytes = lay.total;
-  j.out_key_bytes = s.cap * s.kw * 8;
-  j.out_cnt_bytes = s.cap * 4;
+  j.nf_max = kc::make_shape(shape_opts(p), L, n_reads, k, canonical, j.copy_reads, !off_dev, j.s, j.lay);
+  j.P1 = 1 << j.s.b1;
+  j.ws_bytes = j.lay.total;
+  j.out_key_bytes = j.s.cap * j.s.kw * 8;
+  j.out_cnt_bytes = j.s.cap * 4;
 }
 
 // The buffers of one count with scratch at `ws` and its outputs at j.okeys / j.ocnts.
 kc::Buffers make_buffers(const Job& j, uint8_t* ws) {
-  kc::Buffers b{};
-  b.reads = j.copy_reads ? (const uint8_t*)(ws + j.o_reads) : j.reads;
-  b.offsets = j.off_dev ? j.offsets : (const uint64_t*)(ws + j.o_offs);
-  b.codes64 = (uint64_t*)(ws + j.o_codes);
-  b.inv32 = (uint32_t*)(ws + j.o_inv);
-  b.tile_first = (uint64_t*)(ws + j.o_tf);
-  b.hist = (uint32_t*)(ws + j.o_hist);
-  b.toff = (uint64_t*)(ws + j.o_toff);
-  b.cstart = (uint64_t*)(ws + j.o_cst);
-  b.fine_base = (uint32_t*)(ws + j.o_fb);
-  b.fine_m = (uint32_t*)(ws + j.o_fl);
-  b.hll = (uint32_t*)(ws + j.o_hll);
-  b.fhist = (uint32_t*)(ws + j.o_fh);
-  b.foff = (uint64_t*)(ws + j.o_fo);
-  b.flo = (uint32_t*)(ws + j.o_flo);
-  b.fcur = (unsigned long long*)(ws + j.o_fc);
-  b.look = (unsigned long long*)(ws + j.o_look);
-  b.kbuf = (uint64_t*)(ws + j.o_kbuf);
-  b.sbuf = (uint64_t*)(ws + j.o_sbuf);
-  b.meta = (kc::Meta*)(ws + j.o_meta);
+  kc::Buffers b = kc::layout_buffers(j.lay, ws);
+  if (!j.copy_reads) b.reads = j.reads;
+  if (j.off_dev) b.offsets = j.offsets;
   b.out_keys = (uint64_t*)j.okeys;
   b.out_counts = (uint32_t*)j.ocnts;
   return b;
@@ -314,17 +368,13 @@ bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst,
   const kc::Buffers b = make_buffers(j, ws);
   if (!enqueue_copies(j, b, st, err)) return false;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.fhist, 0, (size_t)j.nf_max * 4, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.look, 0, (size_t)j.nf_max * 8, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.cstart, 0, (size_t)(j.P1 + 1) * 8, st)) != cudaSuccess) {
+  if ((e = (cudaError_t)kc::clear_scratch(s, b, (void*)st)) != cudaSuccess) {
     *err = std::string("clearing scratch: ") + cudaGetErrorString(e);
     return false;
   }
   int l = kc::launch_phase1(s, b, n_sms, (void*)st, mark);
   if (l >= 0) {
-    const int l2 = kc::launch_phase2(s, b, n_sms, j.nf_max, (void*)st, mark);
+    const int l2 = kc::launch_phase2(s, b, n_sms, (void*)st, mark);
     l = l2 >= 0 ? l + l2 : l2;
   }
   if (l < 0) {
@@ -593,8 +643,8 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
     return fail(KC_EINVAL, "kc_plan: alloc and free_ must be given together");
   if (opts->n_partitions_hint && (opts->n_partitions_hint & (opts->n_partitions_hint - 1)))
     return fail(KC_EINVAL, "kc_plan: n_partitions_hint must be a power of two");
-  if (opts->n_partitions_hint > (1u << kc::kMaxCoarseLog2))
-    return fail(KC_EINVAL, "kc_plan: n_partitions_hint above 4096");
+  if (opts->n_partitions_hint > (1u << kc::max_coarse_log2(1)))
+    return fail(KC_EINVAL, "kc_plan: n_partitions_hint above 2048");
   if (opts->table_load < 0.f || opts->table_load > 0.95f) return fail(KC_EINVAL, "kc_plan: table_load outside [0, 0.95]");
   if (opts->table_slots_max && opts->table_slots_max < 64) return fail(KC_EINVAL, "kc_plan: table_slots_max below 64");
   int ndev = 0;
@@ -621,6 +671,7 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->smem_optin = prop.sharedMemPerBlockOptin;
   p->profile = (opts->flags & KC_PLAN_PROFILE) != 0;
   p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
+  p->withhold = (opts->flags & KC_PLAN_TEST_WITHHOLD_PREFIX) != 0;
   p->small_arena = (opts->flags & KC_PLAN_BATCH_ARENA_SMALL) != 0;
   p->aggr = ((opts->flags & KC_PLAN_ABLATE_NO_SMEM_BUCKETS) ? kc::kAggrNoSmemBuckets : 0) |
             ((opts->flags & KC_PLAN_WARP_MERGE) ? kc::kAggrWarpMerge : 0);

@@ -54,9 +54,6 @@ bool device_resident(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-int clog2(uint64_t v) { return v <= 1 ? 0 : 64 - __builtin_clzll(v - 1); }
-
 // One-time set-up on the current device: the scratch array's device address (host code
 // cannot use the symbol itself) and the kernels' shared-memory attributes.
 kc_status setup_device(int dev, DeviceSetup** out) {
@@ -101,6 +98,12 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   cudaStream_t strm = (cudaStream_t)stream;
   if (!device_resident(offsets) || !device_resident(out_keys) || !device_resident(out_counts))
     return nfail(KC_EINVAL, "kc_count_noalloc: offsets and outputs must be device memory");
+  // the kernels read offsets as 8-byte words, write counts as 4-byte words and keys as 8- or
+  // (k > 32) 16-byte words: a misaligned buffer is refused before anything is launched
+  if (((uintptr_t)offsets & 7) != 0 || ((uintptr_t)out_counts & 3) != 0 ||
+      ((uintptr_t)out_keys & (k > 32 ? 15 : 7)) != 0)
+    return nfail(KC_EINVAL, "kc_count_noalloc: offsets must be 8-byte aligned, out_counts 4-byte aligned and out_keys "
+                            "8-byte aligned (16-byte for k > 32)");
   uint64_t first = 0, L = 0;
   if ((e = cudaMemcpyAsync(&first, offsets, 8, cudaMemcpyDeviceToHost, strm)) != cudaSuccess ||
       (e = cudaMemcpyAsync(&L, offsets + n_reads, 8, cudaMemcpyDeviceToHost, strm)) != cudaSuccess ||
@@ -116,85 +119,28 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   if (out_capacity < cap)
     return nfail(KC_EINVAL, "kc_count_noalloc: out_capacity must be at least offsets[n_reads] (the number of bases)");
 
-  // shape: the same choices kc_count makes for this input size
+  // shape and scratch layout: the same choices kc_count makes for this input size
+  kc::ShapeOpts so;
+  so.smem_optin = ds->smem_optin;
+  so.n_sms = ds->n_sms;
   kc::Shape s{};
-  s.L = L;
-  s.n_reads = n_reads;
-  s.n_words = (L + 31) / 32;
-  s.n_tiles = (s.n_words + kc::kTileWords - 1) / kc::kTileWords;
-  s.k = k;
-  s.canonical = canonical ? 1 : 0;
-  s.kw = k <= 32 ? 1 : 2;
-  {
-    const int want = clog2(L / kc::coarse_bases(s.kw) + 1);  // the same rule as kc_count
-    s.b1 = want < 11 ? want : 11;
-  }
-  const int P1 = 1 << s.b1;
-  s.bT_max = kc::table_log2_max(s.kw, ds->smem_optin);
-  s.tail = s.bT_max >= 10 ? 1024 : (1 << s.bT_max);
-  const double ft = (double)(1u << s.bT_max) * 0.55;
-  s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
-  s.cap = cap;
-  const uint64_t nf_bound = cap / s.fine_target + (uint64_t)P1 + 1;
-  const uint64_t nf_lim = (uint64_t)P1 * kc::kMaxFine;
-  const uint32_t nf_max = (uint32_t)(nf_bound < nf_lim ? nf_bound : nf_lim);
-  s.nf_max = nf_max;
-  s.smem_budget = ds->smem_optin;
-  s.profile = 0;
-  s.defer_all = 0;
-
-  // scratch layout inside the static array
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    const size_t at = o;
-    o = up256(o + (bytes ? bytes : 1));
-    return at;
-  };
-  const size_t o_codes = take(s.n_words * 8), o_inv = take(s.n_words * 4), o_tf = take(s.n_tiles * 8);
-  const size_t o_hist = take(s.n_tiles * P1 * 4), o_toff = take(s.n_tiles * P1 * 8);
-  const size_t o_cst = take((size_t)(P1 + 1) * 8), o_fb = take((size_t)(P1 + 1) * 4), o_fl = take((size_t)P1 * 4);
-  const size_t o_hll = take((size_t)kc::kHllRegs * 4);
-  const size_t o_fh = take((size_t)nf_max * 4), o_fo = take((size_t)(nf_max + 1) * 8);
-  const size_t o_flo = take((size_t)(nf_max + 1) * 4);
-  const size_t o_fc = take((size_t)nf_max * 8), o_look = take((size_t)nf_max * 8);
-  const size_t o_kbuf = take(cap * s.kw * 8), o_sbuf = take(cap * s.kw * 8), o_meta = take(sizeof(kc::Meta));
-  if (o > (size_t)KC_NOALLOC_SCRATCH_BYTES)
+  kc::Layout lay{};
+  kc::make_shape(so, L, n_reads, k, canonical, false, false, s, lay);
+  if (lay.total > (size_t)KC_NOALLOC_SCRATCH_BYTES)
     return nfail(KC_EINVAL, "kc_count_noalloc: input needs more scratch than the fixed array holds");
-  uint8_t* ws = (uint8_t*)ds->scratch;
-  kc::Buffers b{};
+  kc::Buffers b = kc::layout_buffers(lay, (uint8_t*)ds->scratch);
   b.reads = reads;
   b.offsets = offsets;
-  b.codes64 = (uint64_t*)(ws + o_codes);
-  b.inv32 = (uint32_t*)(ws + o_inv);
-  b.tile_first = (uint64_t*)(ws + o_tf);
-  b.hist = (uint32_t*)(ws + o_hist);
-  b.toff = (uint64_t*)(ws + o_toff);
-  b.cstart = (uint64_t*)(ws + o_cst);
-  b.fine_base = (uint32_t*)(ws + o_fb);
-  b.fine_m = (uint32_t*)(ws + o_fl);
-  b.hll = (uint32_t*)(ws + o_hll);
-  b.fhist = (uint32_t*)(ws + o_fh);
-  b.foff = (uint64_t*)(ws + o_fo);
-  b.flo = (uint32_t*)(ws + o_flo);
-  b.fcur = (unsigned long long*)(ws + o_fc);
-  b.look = (unsigned long long*)(ws + o_look);
-  b.kbuf = (uint64_t*)(ws + o_kbuf);
-  b.sbuf = (uint64_t*)(ws + o_sbuf);
-  b.meta = (kc::Meta*)(ws + o_meta);
   b.out_keys = out_keys;
   b.out_counts = out_counts;
 
   // the array keeps the previous call's contents: clear what the kernels expect at zero
-  if ((e = cudaMemsetAsync(b.meta, 0, sizeof(kc::Meta), strm)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.fhist, 0, (size_t)nf_max * 4, strm)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.hll, 0, (size_t)kc::kHllRegs * 4, strm)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.look, 0, (size_t)nf_max * 8, strm)) != cudaSuccess ||
-      (e = cudaMemsetAsync(b.cstart, 0, (size_t)(P1 + 1) * 8, strm)) != cudaSuccess)
+  if ((e = (cudaError_t)kc::clear_scratch(s, b, (void*)strm)) != cudaSuccess)
     return nfail(KC_ECUDA, std::string("kc_count_noalloc: clearing scratch: ") + cudaGetErrorString(e));
   kc::Marker none;
   int launches = kc::launch_phase1(s, b, ds->n_sms, (void*)strm, none);
   if (launches >= 0) {
-    const int l2 = kc::launch_phase2(s, b, ds->n_sms, nf_max, (void*)strm, none);
+    const int l2 = kc::launch_phase2(s, b, ds->n_sms, (void*)strm, none);
     launches = l2 >= 0 ? launches + l2 : l2;
   }
   kc::Meta m{};
@@ -204,6 +150,10 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
     return nfail(KC_ECUDA, std::string("kc_count_noalloc: launch: ") + cudaGetErrorString((cudaError_t)(-launches)));
   if (ce != cudaSuccess || se != cudaSuccess)
     return nfail(KC_ECUDA, std::string("kc_count_noalloc: ") + cudaGetErrorString(ce != cudaSuccess ? ce : se));
+  // the status record must describe a result that fits the caller's buffers
+  if (m.n_windows > L || m.n_distinct > m.n_windows || m.n_fine > s.nf_max || m.n_deferred > m.n_fine ||
+      m.n_distinct > out_capacity)
+    return nfail(KC_ECUDA, "kc_count_noalloc: inconsistent status record");
   if (m.status & kc::ST_BAD_OFFSETS) return nfail(KC_EINVAL, "kc_count_noalloc: offsets must be non-decreasing");
   if (m.status & kc::ST_PARTITION_OVERFLOW) return nfail(KC_EOVERFLOW, "kc_count_noalloc: a key range holds 2^32 windows");
   if (m.status & kc::ST_COUNT_OVERFLOW) return nfail(KC_EOVERFLOW, "kc_count_noalloc: a count exceeds 2^32 - 1");

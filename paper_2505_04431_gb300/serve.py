@@ -43,21 +43,22 @@ def footprint(req: Request) -> int:
     return req.n_bases * FOOTPRINT_PER_BASE[1 if req.k <= 32 else 2] + (64 << 20)
 
 
-def _digest(res):
-    """(distinct keys, valid windows, sum of key words, sum of counts) of a device result."""
-    import torch
-    keys = res.keys_tensor()
-    counts = res.counts_tensor()
-    ks = int(keys.sum().item()) if res.n else 0
-    cs = int(counts.to(torch.int64).sum().item()) if res.n else 0
-    return (res.n, res.n_valid_windows, ks, cs)
+def result_digest(res):
+    """(distinct keys, valid windows, SHA-256 of the whole sorted result): two results have
+    the same digest only if they hold the same keys with the same counts, entry by entry."""
+    import hashlib
+    keys, counts = res.to_numpy()
+    h = hashlib.sha256()
+    h.update(keys.tobytes())
+    h.update(counts.tobytes())
+    return (res.n, res.n_valid_windows, h.hexdigest())
 
 
 def _finish(r: Request, res, t_done: float, keep_digest: bool):
     r.done = t_done
     r.n_distinct, r.n_valid = res.n, res.n_valid_windows
     if keep_digest:  # on the current stream: behind any counts still queued there
-        r.digest = _digest(res)
+        r.digest = result_digest(res)
     res.free()
 
 

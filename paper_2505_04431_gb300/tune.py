@@ -9,19 +9,19 @@ No part of the counting happens here: this module only times calls into the libr
 """
 from __future__ import annotations
 
-MAX_PARTITIONS = 4096
+MAX_PARTITIONS = 2048
 TABLE_LOADS = (0.45, 0.55)
 
 
 def _time_count(make_counter, opts, reads, offsets, k, canonical, repeats):
     """(median ms, digest, coarse partitions used) of kc_count under plan options `opts`."""
     import torch
-    from .serve import _digest
+    from .serve import result_digest
     stream = torch.cuda.Stream()
     counter = make_counter(stream=stream, **opts)
     try:
         res = counter.count(reads, offsets, k, canonical)  # warm-up; its digest is the check
-        digest = _digest(res)
+        digest = result_digest(res)
         res.free()
         p1 = counter.stats()["n_partitions"]
         times = []

@@ -143,7 +143,7 @@ def digests_alone(counter, reqs):
     for r in reqs:
         res = counter.count(r.reads, r.offsets, r.k)
         try:
-            out.append(sv._digest(res))
+            out.append(sv.result_digest(res))
         finally:
             res.free()
     return out
