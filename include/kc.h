@@ -57,8 +57,7 @@ typedef struct {
   kc_free_fn free_;           /* NULL: cudaFreeAsync on `stream` */
   void *alloc_ctx;            /* passed back to alloc / free_ */
   uint64_t max_device_bytes;  /* 0: no limit; else kc_count fails with KC_ENOMEM above it */
-  uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 2048; at most 1024 are used for
-                                 k > 32); 0: chosen from input size */
+  uint32_t n_partitions_hint; /* coarse partitions (power of two, <= 4096); 0: chosen from input size */
   uint32_t block_size_hint;   /* reserved (0) */
   float table_load;           /* distinct keys aimed at per fine partition, as a fraction of the
                                  count table's slots (the fine split is sized by it); 0: 0.55 */
@@ -70,9 +69,9 @@ typedef struct {
 /* kc_plan_opts.flags: record a CUDA event on the plan's stream after every kernel
  * launch of kc_count, so kc_last_kernel_times can report each kernel's device time. */
 #define KC_PLAN_PROFILE 1u
-/* Testing: every fine partition leaves its sorted run in its thread block's stage and
- * writes it out later (the path taken when a partition's output offset is not yet known
- * when it is ready to write). */
+/* Testing: every fine partition writes its run to its own input region and the final
+ * compaction pass moves it (the path taken when a partition's output offset is not yet
+ * known when it is ready to write). */
 #define KC_PLAN_DEFER_ALL 2u
 /* Testing: kc_count_batch's scratch arena (counts that share batched launches) is limited
  * to 32 MiB, so that small batches form several groups and larger counts run alone. */
@@ -91,6 +90,9 @@ typedef struct {
  * wait for it is cut to a few iterations, so that the later partitions' bounded waits run
  * out: kc_count then returns KC_ETIMEOUT (no GPU fault, no hang). */
 #define KC_PLAN_TEST_WITHHOLD_PREFIX 32u
+/* Testing: counts above 2^16 - 1 are reported as overflowing (KC_EOVERFLOW), so that the
+ * overflow report can be checked without an input of 2^32 windows of one k-mer. */
+#define KC_PLAN_TEST_COUNT_LIMIT 64u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */
@@ -191,7 +193,7 @@ kc_status kc_last_kernel_times(kc_plan_t plan, uint32_t max, const char **names,
  * out_capacity, bad k or offsets), KC_ECUDA, KC_EOVERFLOW, KC_ETIMEOUT; kc_last_error()
  * gives the message. */
 #define KC_NOALLOC_MAX_BASES (1u << 20)
-#define KC_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define KC_NOALLOC_SCRATCH_BYTES (48u << 20)
 kc_status kc_count_noalloc(const uint8_t *reads, const uint64_t *offsets, uint64_t n_reads, int k, int canonical,
                            uint64_t *out_keys, uint32_t *out_counts, uint64_t out_capacity, uint64_t *n_distinct,
                            uint64_t *n_valid_windows, void *stream);

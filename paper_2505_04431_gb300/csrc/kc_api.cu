@@ -59,23 +59,27 @@ uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int
   s.k = k;
   s.canonical = canonical ? 1 : 0;
   s.kw = k <= 32 ? 1 : 2;
-  const int bmax = max_coarse_log2(s.kw);
   int b1;
   if (o.p_hint) {
     b1 = ceil_log2_u64(o.p_hint);
   } else {
-    // coarse partitions of about 3 Mi bases (64-bit keys) or 1.5 Mi (128-bit keys): a
-    // coarse partition's keys and their split copy stay in L2 while phase 2 works on them
-    b1 = ceil_log2_u64(L / coarse_bases(s.kw) + 1);
+    // coarse partitions of at most about 12 Mi windows (64-bit keys) or 6 Mi (128-bit keys):
+    // few enough partitions that pass B's per-partition runs stay long, small enough that a
+    // partition of distinct keys splits into at most ~2800 (64-bit) or ~1400 (128-bit) fine
+    // partitions of one table each, within kMaxFine (measured on GB300: 256 coarse
+    // partitions for 3 G bases of 64-bit keys beat 512 and 128)
+    const int want = ceil_log2_u64(L / coarse_bases(s.kw) + 1);
+    b1 = want < 11 ? want : 11;
   }
-  s.b1 = b1 < bmax ? b1 : bmax;
-  const uint64_t P1 = 1ull << s.b1;
-  int bT_max = table_log2_max(s.kw, o.smem_optin);
+  s.b1 = b1;
+  const uint64_t P1 = 1ull << b1;
+  int bT_max = table_log2_max(s.kw, o.smem_optin, o.smem_per_sm);
   if (o.slots_max) {
     const int bt = 63 - __builtin_clzll((uint64_t)o.slots_max);
     if (bt < bT_max) bT_max = bt;
   }
   s.bT_max = bT_max;
+  s.tail = bT_max >= 10 ? 1024 : (1 << bT_max);
   const double ft = (double)(1u << bT_max) * o.load;  // distinct keys per fine partition aimed at
   s.fine_target = ft < 16 ? 16u : (uint32_t)ft;
   s.cap = L > 0 ? L : 1;
@@ -83,22 +87,9 @@ uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int
   const uint64_t nf_bound = s.cap / s.fine_target + P1 + 1;
   const uint64_t nf_lim = P1 * kMaxFine;
   s.nf_max = nf_bound < nf_lim ? nf_bound : nf_lim;
-  // run starts: (m_c + 1) per chunk, m_c <= kMaxFine, at most K / chunk + P1 chunks
-  s.tcap = ((uint64_t)kMaxFine + 1) * (s.cap / split_chunk(s.kw) + P1);
-  // one stage slot per phase-2 block: a block per 8 Ki bases, at most one per SM
-  const uint64_t want_blocks = (L + 8191) / 8192;
-  const uint64_t sms = o.n_sms > 0 ? (uint64_t)o.n_sms : 1;
-  s.n_stage = (uint32_t)(want_blocks < 1 ? 1 : (want_blocks > sms ? sms : want_blocks));
-  // stage slots per block: a partition whose prefix is late waits in a slot; several slots
-  // let a block go on while a slow partition further back holds the prefixes up (at most
-  // a quarter of the block's expected fine partitions)
-  {
-    const uint64_t per = s.nf_max / s.n_stage / 4;
-    s.n_slots = (uint32_t)(per < 1 ? 1 : (per > (uint64_t)kMaxSlots ? (uint64_t)kMaxSlots : per));
-  }
-  s.stage_bytes = (uint32_t)stage_slot_bytes(s.kw, bT_max);
-  s.spin_limit = o.withhold ? kTestSpinLimit : kLookbackSpinLimit;
   s.smem_budget = o.smem_optin;
+  s.spin_limit = o.withhold ? kTestSpinLimit : kLookbackSpinLimit;
+  s.count_limit = o.low_count_limit ? kTestCountLimit : 0xffffffffu;
   s.profile = o.profile;
   s.defer_all = o.defer_all;
   s.withhold = o.withhold;
@@ -122,14 +113,10 @@ uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int
   lay.fm = take(P1 * 4);
   lay.hll = take((size_t)kHllRegs * 4);
   lay.fh = take(nf * 4);
+  lay.fo = take((nf + 1) * 8);
   lay.flo = take((nf + 1) * 4);
+  lay.fc = take(nf * 8);
   lay.look = take(nf * 8);
-  lay.tstart = take((P1 + kStageLag + 1) * 4);
-  lay.tsplit = take((P1 + kStageLag) * 4);
-  lay.tbase = take((P1 + 1) * 8);
-  lay.rstart = take(s.tcap * 2);
-  lay.sdone = take(P1 * 4);
-  lay.stage = take((size_t)s.n_stage * s.n_slots * s.stage_bytes);
   lay.kbuf = take(s.cap * s.kw * 8);
   lay.sbuf = take(s.cap * s.kw * 8);
   lay.meta = take(sizeof(Meta));
@@ -151,21 +138,16 @@ Buffers layout_buffers(const Layout& lay, uint8_t* ws) {
   b.fine_m = (uint32_t*)(ws + lay.fm);
   b.hll = (uint32_t*)(ws + lay.hll);
   b.fhist = (uint32_t*)(ws + lay.fh);
+  b.foff = (uint64_t*)(ws + lay.fo);
   b.flo = (uint32_t*)(ws + lay.flo);
+  b.fcur = (unsigned long long*)(ws + lay.fc);
   b.look = (unsigned long long*)(ws + lay.look);
-  b.tstart = (uint32_t*)(ws + lay.tstart);
-  b.tsplit = (uint32_t*)(ws + lay.tsplit);
-  b.tbase = (uint64_t*)(ws + lay.tbase);
-  b.rstart = (uint16_t*)(ws + lay.rstart);
-  b.sdone = (uint32_t*)(ws + lay.sdone);
-  b.stage = ws + lay.stage;
   b.kbuf = (uint64_t*)(ws + lay.kbuf);
   b.sbuf = (uint64_t*)(ws + lay.sbuf);
   b.meta = (Meta*)(ws + lay.meta);
   return b;
 }
 
-// The arrays the kernels expect zeroed at the start of a count (stream-ordered).
 int clear_scratch(const Shape& s, const Buffers& b, void* stream) {
   const cudaStream_t st = (cudaStream_t)stream;
   const size_t P1 = (size_t)1 << s.b1;
@@ -174,8 +156,7 @@ int clear_scratch(const Shape& s, const Buffers& b, void* stream) {
   if ((e = cudaMemsetAsync(b.fhist, 0, (size_t)s.nf_max * 4, st)) != cudaSuccess) return (int)e;
   if ((e = cudaMemsetAsync(b.hll, 0, (size_t)kHllRegs * 4, st)) != cudaSuccess) return (int)e;
   if ((e = cudaMemsetAsync(b.look, 0, (size_t)s.nf_max * 8, st)) != cudaSuccess) return (int)e;
-  if ((e = cudaMemsetAsync(b.cstart, 0, (P1 + 1) * 8, st)) != cudaSuccess) return (int)e;
-  return (int)cudaMemsetAsync(b.sdone, 0, P1 * 4, st);
+  return (int)cudaMemsetAsync(b.cstart, 0, (P1 + 1) * 8, st);
 }
 }  // namespace kc
 
@@ -191,6 +172,7 @@ struct kc_plan_s {
   uint32_t slots_max = 0;
   int n_sms = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // batched counts: scratch arena of a group of counts, device and pinned host tables
@@ -222,6 +204,7 @@ struct kc_plan_s {
   bool profile = false;
   bool defer_all = false;
   bool withhold = false;
+  bool low_count_limit = false;
   bool small_arena = false;
   int aggr = 0;
   static constexpr int kMaxMarks = 32;
@@ -310,10 +293,11 @@ kc::ShapeOpts shape_opts(const kc_plan_s* p) {
   o.load = p->load;
   o.slots_max = p->slots_max;
   o.smem_optin = p->smem_optin;
-  o.n_sms = p->n_sms;
+  o.smem_per_sm = p->smem_per_sm;
   o.profile = p->profile ? 1 : 0;
   o.defer_all = p->defer_all ? 1 : 0;
   o.withhold = p->withhold ? 1 : 0;
+  o.low_count_limit = p->low_count_limit ? 1 : 0;
   o.aggr = p->aggr;
   return o;
 }
@@ -374,7 +358,7 @@ bool enqueue_job(const Job& j, uint8_t* ws, cudaStream_t st, kc::Meta* meta_dst,
   }
   int l = kc::launch_phase1(s, b, n_sms, (void*)st, mark);
   if (l >= 0) {
-    const int l2 = kc::launch_phase2(s, b, n_sms, (void*)st, mark);
+    const int l2 = kc::launch_phase2(s, b, n_sms, j.nf_max, (void*)st, mark);
     l = l2 >= 0 ? l + l2 : l2;
   }
   if (l < 0) {
@@ -405,7 +389,7 @@ kc_status job_status(const Job& j, const kc::Meta& m, const char* who, std::stri
     return KC_EOVERFLOW;
   }
   if (m.status & kc::ST_COUNT_OVERFLOW) {
-    *msg = w + ": a count exceeds 2^32 - 1";
+    *msg = w + (j.s.count_limit == 0xffffffffu ? ": a count exceeds 2^32 - 1" : ": a count exceeds the test limit");
     return KC_EOVERFLOW;
   }
   if (m.status & kc::ST_TIMEOUT) {
@@ -643,8 +627,8 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
     return fail(KC_EINVAL, "kc_plan: alloc and free_ must be given together");
   if (opts->n_partitions_hint && (opts->n_partitions_hint & (opts->n_partitions_hint - 1)))
     return fail(KC_EINVAL, "kc_plan: n_partitions_hint must be a power of two");
-  if (opts->n_partitions_hint > (1u << kc::max_coarse_log2(1)))
-    return fail(KC_EINVAL, "kc_plan: n_partitions_hint above 2048");
+  if (opts->n_partitions_hint > (1u << kc::kMaxCoarseLog2))
+    return fail(KC_EINVAL, "kc_plan: n_partitions_hint above 4096");
   if (opts->table_load < 0.f || opts->table_load > 0.95f) return fail(KC_EINVAL, "kc_plan: table_load outside [0, 0.95]");
   if (opts->table_slots_max && opts->table_slots_max < 64) return fail(KC_EINVAL, "kc_plan: table_slots_max below 64");
   int ndev = 0;
@@ -669,9 +653,11 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->slots_max = opts->table_slots_max;
   p->n_sms = prop.multiProcessorCount;
   p->smem_optin = prop.sharedMemPerBlockOptin;
+  p->smem_per_sm = prop.sharedMemPerMultiprocessor;
   p->profile = (opts->flags & KC_PLAN_PROFILE) != 0;
   p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
   p->withhold = (opts->flags & KC_PLAN_TEST_WITHHOLD_PREFIX) != 0;
+  p->low_count_limit = (opts->flags & KC_PLAN_TEST_COUNT_LIMIT) != 0;
   p->small_arena = (opts->flags & KC_PLAN_BATCH_ARENA_SMALL) != 0;
   p->aggr = ((opts->flags & KC_PLAN_ABLATE_NO_SMEM_BUCKETS) ? kc::kAggrNoSmemBuckets : 0) |
             ((opts->flags & KC_PLAN_WARP_MERGE) ? kc::kAggrWarpMerge : 0);

@@ -10,11 +10,7 @@
 //   kbuf         keys grouped by coarse partition (the owner partition of
 //                Algorithm 3's AsyncAdd, here a key range so that outputs concatenate
 //                in sorted order).
-//   sbuf         the same keys, each split chunk of a coarse partition regrouped by
-//                fine partition in place (chunk j of coarse partition c covers kbuf /
-//                sbuf positions cstart[c] + j * chunk ..); rstart[] holds where each
-//                fine partition's run starts inside each chunk.
-//   stage        deferred runs, n_slots per phase-2 thread block (keys, then counts).
+//   sbuf         the same keys regrouped by fine partition inside each coarse one.
 //   out keys / counts   the sorted histogram.
 #pragma once
 #include <stdint.h>
@@ -25,32 +21,28 @@ constexpr int kWordBases = 32;                 // bases per packed code word
 constexpr int kTileWords = 8192;               // one phase-1 tile = 262144 bases
 constexpr uint64_t kTileBases = (uint64_t)kTileWords * kWordBases;
 constexpr int kPackThreads = 512;              // pass A: one code word per thread per sub-step
-// most coarse partitions: the phase-2 kernel keeps two words per coarse partition in
-// shared memory next to its largest count table
-__host__ __device__ constexpr int max_coarse_log2(int kw) { return kw == 1 ? 11 : 10; }
-constexpr int kMaxFine = 1024;                 // at most this many fine partitions per coarse one
-// bases per coarse partition aimed at when the plan sets no partition count: a coarse
-// partition's keys (about 19 MB of 64-bit or 128-bit keys) and their split copy stay in L2
-// while phase 2 works on them
-constexpr uint64_t coarse_bases(int kw) { return kw == 1 ? (3ull << 20) : (3ull << 19); }
-constexpr int kCountThreads = 1024;            // phase-2 CTA
-constexpr int kSplitSubs = 4;                  // sub-chunks (one shared-memory staging each) per split task
-__host__ __device__ constexpr uint32_t split_sub(int kw) { return kw == 1 ? 8192u : 4096u; }
-__host__ __device__ constexpr uint32_t split_chunk(int kw) { return split_sub(kw) * kSplitSubs; }
-constexpr int kRunBatch = 256;                 // runs of a fine partition held in shared memory at once
-constexpr int kMaxSlots = 8;                   // deferred runs one phase-2 block may hold at once
-// phase-2 tickets: the count tasks of coarse partition c come kStageLag stages after its
-// split tasks, so that those have finished when the count tasks start
-#ifndef KC_STAGE_LAG
-#define KC_STAGE_LAG 2
+constexpr int kMaxCoarseLog2 = 12;             // at most 4096 coarse partitions
+constexpr int kMaxFine = 4096;                 // at most this many fine partitions per coarse one
+// bases per coarse partition aimed at when the plan sets no partition count
+constexpr uint64_t coarse_bases(int kw) { return kw == 1 ? (12ull << 20) : (6ull << 20); }
+// count kernel: threads per block and blocks per SM (one block of 1024 threads with
+// 8192-slot tables, or two of 512 threads with 4096-slot tables)
+#ifndef KC_COUNT_THREADS
+#define KC_COUNT_THREADS 1024
 #endif
-constexpr int kStageLag = KC_STAGE_LAG;
+constexpr int kCountThreads = KC_COUNT_THREADS;
+constexpr int kCountBlocksPerSM = 1024 / kCountThreads;
+static_assert(kCountThreads == 1024 || kCountThreads == 512, "count blocks of 1024 or 512 threads");
+constexpr int kFineChunk1 = 8192;              // fine-scatter chunk, 64-bit keys
+constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit keys
+constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
 constexpr int kHllLog2 = 10;                   // distinct-key sketch: 1024 registers
 constexpr int kHllRegs = 1 << kHllLog2;
 constexpr int kHllSampleLog2 = 3;              // ... over a 1/8 hash sample of the keys
 constexpr double kHllSample = 8.0;
 constexpr uint32_t kLookbackSpinLimit = 1u << 22;  // x ~100 ns sleep: ~0.4 s, then give up
 constexpr uint32_t kTestSpinLimit = 64;            // the same wait when a test withholds a prefix
+constexpr uint32_t kTestCountLimit = 0xffff;       // the count limit when a test lowers it
 
 // status bits written by kernels (a kc_status is derived from them on the host)
 enum : uint32_t {
@@ -67,14 +59,13 @@ struct Meta {
   uint64_t n_distinct;  // D
   uint64_t n_fine;      // number of fine partitions
   uint64_t n_overflow;  // fine partitions that took the overflow path
-  uint64_t n_deferred;  // fine partitions whose run waited in the stage (prefix unknown in time)
+  uint64_t n_deferred;  // fine partitions written out by k_compact (prefix unknown in time)
   uint32_t status;
   uint32_t pad;
   uint64_t ticket;      // phase-2 work counter
-  uint64_t n_tasks;     // phase-2 tasks (split chunks and fine partitions)
   uint64_t d_estimate;  // distinct keys estimated by the sketch
-  uint64_t sub_cycles[8];    // profiled plans only: phase-2 task counts (split, count, count tasks that waited)
-  uint64_t phase_cycles[8];  // profiled plans only: SM cycles per phase-2 phase, summed over thread blocks
+  uint64_t sub_cycles[8];    // profiled plans only: ordering sub-steps (range, rank, scan, place, small sorts, big sorts, #big)
+  uint64_t phase_cycles[8];  // profiled plans only: SM cycles per phase of k_count_emit, summed over CTAs
 };
 
 struct Shape {
@@ -87,17 +78,15 @@ struct Shape {
   int kw;               // key words: 1 or 2
   int b1;               // log2 coarse partitions
   int bT_max;           // log2 of the largest table
+  int tail;             // table slots past the home range (linear probing never wraps)
   uint32_t fine_target; // keys per fine partition aimed for
   uint64_t cap;         // capacity of kbuf / sbuf / outputs in keys
   uint64_t nf_max;      // capacity of the fine-partition arrays
   uint64_t smem_budget; // opt-in shared memory per block
-  uint64_t tcap;        // capacity of the run-start table (16-bit entries)
-  uint32_t n_stage;     // phase-2 blocks with stage slots (the phase-2 grid is at most this)
-  uint32_t n_slots;     // stage slots of each of them (1 .. kMaxSlots)
-  uint32_t stage_bytes; // bytes of one stage slot
   uint32_t spin_limit;  // iterations of a bounded device wait before it gives up
-  int profile;          // nonzero: the phase-2 kernel accumulates per-phase cycle counts
-  int defer_all;        // nonzero (testing): every fine partition's run waits in the stage
+  uint32_t count_limit; // largest count reported (2^32 - 1; lower only when a test asks)
+  int profile;          // nonzero: k_count_emit accumulates per-phase cycle counts
+  int defer_all;        // nonzero (testing): every fine partition takes the deferred write-out
   int withhold;         // nonzero (testing): partition 0 never publishes its prefix
   int aggr;             // aggregation variants: kAggr* bits (single-count path only)
 };
@@ -116,16 +105,11 @@ struct Buffers {
   uint32_t* fine_base;    // [P1 + 1] first fine index of each coarse partition
   uint32_t* fine_m;       // [P1] fine partitions of each coarse partition
   uint32_t* hll;          // [kHllRegs] distinct-key sketch (max-merged by pass B)
-  uint32_t* fhist;        // [nf_max] distinct keys of each fine partition
+  uint32_t* fhist;        // [nf_max] keys per fine partition (fine split); then distinct keys | deferred bit 31
+  uint64_t* foff;         // [nf_max + 1] fine partition starts
   uint32_t* flo;          // [nf_max + 1] first range-map value u of each fine partition (0 after the last)
+  unsigned long long* fcur;  // [nf_max] fine scatter cursors
   unsigned long long* look;  // [nf_max] look-back status words
-  uint32_t* tstart;       // [P1 + kStageLag + 1] first phase-2 ticket of each stage (stage s: split
-                          // tasks of coarse partition s, then count tasks of partition s - kStageLag)
-  uint32_t* tsplit;       // [P1 + kStageLag] first count ticket of each stage
-  uint64_t* tbase;        // [P1 + 1] first run-start entry of each coarse partition
-  uint16_t* rstart;       // [tcap] coarse partition c: entry (f, j) at tbase[c] + f * chunks(c) + j
-  uint32_t* sdone;        // [P1] finished split tasks of each coarse partition
-  uint8_t* stage;         // [n_stage * n_slots * stage_bytes] deferred runs
   uint64_t* kbuf;
   uint64_t* sbuf;
   uint64_t* out_keys;
@@ -161,8 +145,8 @@ struct BatchPlan {
   uint32_t grid[16] = {};
 };
 enum BatchKernel {
-  BK_CLEAR, BK_CHECK, BK_TILE_FIRST, BK_PACK, BK_COL_SCAN, BK_BUCKET_SCAN, BK_SCATTER, BK_FINE_PLAN, BK_PHASE2,
-  BK_SCAN_DISTINCT, BK_N
+  BK_CLEAR, BK_CHECK, BK_TILE_FIRST, BK_PACK, BK_COL_SCAN, BK_BUCKET_SCAN, BK_SCATTER, BK_FINE_PLAN, BK_FINE_HIST,
+  BK_FINE_SCAN, BK_FINE_SCATTER, BK_COUNT, BK_SCAN_DISTINCT, BK_COMPACT, BK_N
 };
 
 // Called after every kernel launch with the kernel's name (used for per-kernel timing).
@@ -177,7 +161,7 @@ struct Marker {
 // Host launch wrappers (kc_kernels.cu).  Each returns the number of kernel launches, or
 // -cudaError_t if a launch failed (no later kernel is launched then).
 int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, const Marker& mark);
-int launch_phase2(const Shape& s, const Buffers& b, int n_sms, void* stream, const Marker& mark);
+int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, void* stream, const Marker& mark);
 // Blocks each kernel of a batched launch gives one count (host rule, shared by the planner
 // and the launcher), and the whole batched launch sequence (returns launches or
 // -cudaError_t).
@@ -185,31 +169,30 @@ uint32_t batch_blocks(BatchKernel k, const Shape& s, int n_sms, uint64_t bases_t
 int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mark);
 int configure_kernels(int device);  // sets shared-memory attributes; returns 0 or a cudaError_t
 
-size_t phase2_smem(int kw, int bT_max);
+size_t count_kernel_smem(int kw, int bT_max, int tail);
 void set_error_message(const char* msg);  // the text kc_last_error returns on this thread
-int table_log2_max(int kw, size_t smem_optin);
-size_t stage_slot_bytes(int kw, int bT_max);
+int table_log2_max(int kw, size_t smem_optin, size_t smem_per_sm);
 
 // Shape and scratch layout of one count (host only; shared by kc_count, the batched and
-// submitted forms and kc_count_noalloc).  Byte offsets into the count's scratch block.
+// submitted forms and kc_count_noalloc, so that all make the same choices).
 struct ShapeOpts {
   uint32_t p_hint = 0;      // coarse partitions (power of two) or 0
   float load = 0.55f;       // table load aimed at per fine partition
   uint32_t slots_max = 0;   // largest count table (slots) or 0
   size_t smem_optin = 0;
-  int n_sms = 0;
-  int profile = 0, defer_all = 0, withhold = 0, aggr = 0;
+  size_t smem_per_sm = 0;   // shared memory of one SM (for the count blocks it holds)
+  int profile = 0, defer_all = 0, withhold = 0, low_count_limit = 0, aggr = 0;
 };
-struct Layout {
-  size_t reads, offs, codes, inv, tf, hist, toff, cst, fb, fm, hll, fh, flo, look, tstart, tsplit, tbase, rstart,
-      sdone, stage, kbuf, sbuf, meta;
+struct Layout {  // byte offsets into the count's scratch block
+  size_t reads, offs, codes, inv, tf, hist, toff, cst, fb, fm, hll, fh, fo, flo, fc, look, kbuf, sbuf, meta;
   size_t total;
 };
 // Fills s and lay for L bases and n_reads reads; copy_reads / copy_offs: the scratch holds a
-// copy of the reads (L + 16 bytes) / the offsets.  Returns the number of fine-partition
-// entries (nf_max).
+// copy of the reads (L + 16 bytes) / the offsets.  Returns the fine-partition capacity.
 uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int canonical, bool copy_reads,
                     bool copy_offs, Shape& s, Layout& lay);
+// The scratch-held buffers at ws (reads, offsets and outputs are the caller's to set when
+// they are not copies).
 Buffers layout_buffers(const Layout& lay, uint8_t* ws);
 // Enqueue the clears every count starts from on `stream` (a cudaStream_t); returns a
 // cudaError_t.

@@ -14,23 +14,21 @@
 //                           Section IV-C / Algorithm 4 (AddToL2Buffer), which exist to
 //                           turn many small sends into few large ones.
 // Phase 2 (Algorithm 3 after the barrier: Sort + Accumulate; Section V "Phase 2"):
-//   k_fine_plan             sizes the fine partitions of every coarse partition (one
-//                           shared-memory table each, from a HyperLogLog estimate of the
-//                           distinct keys) and lays out the phase-2 tasks.
-//   k_phase2                persistent; takes the coarse partitions in turn: split tasks
-//                           regroup a coarse partition's keys by fine partition chunk by
-//                           chunk, count tasks count each fine partition in a hashed
+//   k_fine_plan, k_fine_hist, k_fine_scan, k_fine_scatter   split every owner partition
+//                           into fine partitions small enough for one shared-memory table
+//                           (sized from a HyperLogLog estimate of the distinct keys).
+//   k_count_emit            persistent; per fine partition: count every key in a hashed
 //                           open-addressing table in shared memory (CAS claims a slot, a
 //                           32-bit atomic add counts), order the occupied slots by a
-//                           bucketed counting sort over the partition's key range and
+//                           bucketed counting sort over the partition's key range, and
 //                           write the sorted (key, count) run at the offset found by a
-//                           decoupled look-back (or later, from the block's stage slot).
-//                           A coarse partition's keys pass between its split and count
-//                           tasks through L2 only.
-//   k_scan_distinct         checks every partition's published prefix; the output size.
+//                           decoupled look-back over the fine partitions, or in its own
+//                           input region when that offset is not known in time.
+//   k_scan_distinct, k_compact   output offsets of all runs; the runs written in place
+//                           move to their offsets.
 // Variants: every kernel body also runs as a batched kernel (one launch for a group of
 // counts, each thread block working for one count found through a block table); pass B
-// without the shared-memory staging (DIRECT) and the count tasks with a warp-level merge
+// without the shared-memory staging (DIRECT) and the count kernel with a warp-level merge
 // of equal keys (the heavy-hitter pre-aggregation of Section IV-D; slower on GB300, so off
 // by default) exist for the aggregation experiment of Section VI.
 //
@@ -126,6 +124,17 @@ __device__ __forceinline__ void st_status(unsigned long long* p, unsigned long l
 __device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Two adjacent 64-bit words of shared memory in one 16-byte load, read fresh (volatile):
+// other threads of the block may be claiming them.
+__device__ __forceinline__ ulonglong2 ld_pair_shared(const uint64_t* p) {
+  ulonglong2 v;
+  asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];"
+               : "=l"(v.x), "=l"(v.y)
+               : "r"((uint32_t)__cvta_generic_to_shared(p))
+               : "memory");
   return v;
 }
 
@@ -232,9 +241,8 @@ __device__ T block_exclusive_scan_pad(T* data, int n, T* warp_tmp) {
 }
 
 // ------------------------------------------------------------------ input checks
-// Batched launches: the arrays a count needs zeroed (status record, distinct counts,
-// look-back words, sketch, partition starts, split counters) are cleared by one kernel for
-// all counts.
+// Batched launches: the arrays a count needs zeroed (status record, fine histogram,
+// look-back words, sketch, partition starts) are cleared by one kernel for all counts.
 __global__ void k_clear_batch(BatchTab t) {
   KC_BATCH_PROLOGUE(t);
   const Shape& s = d.s;
@@ -246,7 +254,6 @@ __global__ void k_clear_batch(BatchTab t) {
   }
   for (uint64_t i = i0; i < (uint64_t)kHllRegs; i += stride) b.hll[i] = 0;
   for (uint64_t i = i0; i <= (1ull << s.b1); i += stride) b.cstart[i] = 0;
-  for (uint64_t i = i0; i < (1ull << s.b1); i += stride) b.sdone[i] = 0;
   for (uint64_t i = i0; i < sizeof(Meta) / 4; i += stride) reinterpret_cast<uint32_t*>(b.meta)[i] = 0;
 }
 
@@ -694,28 +701,20 @@ __global__ void k_bucket_scan_batch(BatchTab t) {
   bucket_scan_body(d.b.cstart, d.b.cstart, 1 << d.s.b1, d.b.meta);
 }
 
-// Plan of phase 2, after pass B (one block).  The distinct-key estimate (a sampled
+// Fine split of every coarse partition, after pass B: the distinct-key estimate (a sampled
 // HyperLogLog filled by pass B) gives the duplication factor K / D, and a fine partition
-// aims at fine_target distinct keys, i.e. fine_target * K / D keys: coarse partition c is
-// cut into m_c = ceil(n_c / target) parts of its range of u (at most kMaxFine) and split in
-// ceil(n_c / split_chunk) chunks.  Written here: each fine partition's first value of u
-// (flo), each coarse partition's first fine partition and first run-start entry, and the
-// ticket layout (stage s: the split tasks of coarse partition s, then the count tasks of
-// coarse partition s - 1).
-__device__ __forceinline__ void fine_plan_body(const Shape& s, const Buffers& b) {
-  extern __shared__ uint64_t fsc[];  // [P1 + kStageLag + 1]
+// aims at fine_target distinct keys, i.e. fine_target * K / D keys.  One block.
+__device__ __forceinline__ void fine_plan_body(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
+                            uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
+  extern __shared__ uint64_t fsc[];  // [P1]
   __shared__ uint64_t wt[32];
   __shared__ float zsum_s[32], zeros_s[32];
   __shared__ double target_s;
-  const int P1 = 1 << s.b1, b1 = s.b1;
-  const uint64_t CH = split_chunk(s.kw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  Meta* meta = b.meta;
-  const uint64_t* cstart = b.cstart;
   // HyperLogLog estimate over the 1/8 hash-sample of the keys
   float z = 0.f, zeros = 0.f;
   for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) {
-    const uint32_t r = b.hll[i];
+    const uint32_t r = hll[i];
     z += exp2f(-(float)r);
     zeros += r == 0 ? 1.f : 0.f;
   }
@@ -742,78 +741,50 @@ __device__ __forceinline__ void fine_plan_body(const Shape& s, const Buffers& b)
     const double K = (double)cstart[P1];
     double dup = d_est > 1.0 ? K / d_est : 1.0;
     dup = dup < 1.0 ? 1.0 : (dup > 32.0 ? 32.0 : dup);
-    target_s = (double)s.fine_target * (0.9 * dup > 1.0 ? 0.9 * dup : 1.0);
+    target_s = (double)fine_target * (0.9 * dup > 1.0 ? 0.9 * dup : 1.0);
     meta->d_estimate = (uint64_t)d_est;
   }
   __syncthreads();
   const double target = target_s;
-  // fine partitions per coarse partition, and their first index
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x) {
-    uint64_t m = 0;
-    if (c < P1) {
-      const uint64_t n = cstart[c + 1] - cstart[c];
-      m = (uint64_t)ceil((double)n / target);
-      m = m < 1 ? 1 : (m > (uint64_t)kMaxFine ? (uint64_t)kMaxFine : m);
-      b.fine_m[c] = (uint32_t)m;
-    }
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) {
+    const uint64_t n = cstart[c + 1] - cstart[c];
+    uint64_t m = (uint64_t)ceil((double)n / target);
+    m = m < 1 ? 1 : (m > (uint64_t)kMaxFine ? (uint64_t)kMaxFine : m);
+    fine_m[c] = (uint32_t)m;
     fsc[c] = m;
   }
   __syncthreads();
-  const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1 + 1, wt);
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x) b.fine_base[c] = (uint32_t)fsc[c];
+  const uint64_t NF = block_exclusive_scan<uint64_t>(fsc, P1, wt);
+  for (int c = threadIdx.x; c < P1; c += blockDim.x) fine_base[c] = (uint32_t)fsc[c];
   // fine partition g = fsc[c] + f holds the values u of coarse field c whose low part
   // v = u mod 2^(32 - b1) has floor(v m / 2^(32 - b1)) = f, i.e. v >= ceil(f 2^(32 - b1) / m);
   // one thread per fine partition, its coarse partition found by binary search in fsc
   const uint64_t w = 1ull << (32 - b1);
-  for (uint64_t g = threadIdx.x; g < NF && g < s.nf_max; g += blockDim.x) {
+  for (uint64_t g = threadIdx.x; g < NF && g < nf_max; g += blockDim.x) {
     int lo = 0, hi = P1 - 1;  // last c with fsc[c] <= g
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (fsc[mid] <= g) lo = mid;
       else hi = mid - 1;
     }
-    const uint64_t m = b.fine_m[lo], f = g - fsc[lo];
-    b.flo[g] = (uint32_t)((uint64_t)lo << (32 - b1)) + (uint32_t)((f * w + m - 1) / m);
-  }
-  __syncthreads();
-  // run-start entries: (m_c + 1) per chunk of coarse partition c
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x) {
-    uint64_t e = 0;
-    if (c < P1) e = ((uint64_t)b.fine_m[c] + 1) * ((cstart[c + 1] - cstart[c] + CH - 1) / CH);
-    fsc[c] = e;
-  }
-  __syncthreads();
-  const uint64_t TE = block_exclusive_scan<uint64_t>(fsc, P1 + 1, wt);
-  for (int c = threadIdx.x; c <= P1; c += blockDim.x) b.tbase[c] = fsc[c];
-  __syncthreads();
-  // tickets: stage s = split tasks of s (s < P1), then count tasks of s - kStageLag
-  const int NS = P1 + kStageLag;  // stages
-  for (int c = threadIdx.x; c <= NS; c += blockDim.x) {
-    uint64_t v = 0;
-    if (c < P1) v += (cstart[c + 1] - cstart[c] + CH - 1) / CH;
-    if (c >= kStageLag && c < NS) v += b.fine_m[c - kStageLag];
-    fsc[c] = v;
-  }
-  __syncthreads();
-  const uint64_t T = block_exclusive_scan<uint64_t>(fsc, NS + 1, wt);
-  const bool ok = NF <= s.nf_max && TE <= s.tcap && T < 0xffffffffull;
-  for (int c = threadIdx.x; c < NS; c += blockDim.x) {
-    b.tstart[c] = ok ? (uint32_t)fsc[c] : 0u;
-    const uint64_t nch = c < P1 ? (cstart[c + 1] - cstart[c] + CH - 1) / CH : 0;
-    b.tsplit[c] = ok ? (uint32_t)(fsc[c] + nch) : 0u;
+    const uint64_t m = fine_m[lo], f = g - fsc[lo];
+    flo[g] = (uint32_t)((uint64_t)lo << (32 - b1)) + (uint32_t)((f * w + m - 1) / m);
   }
   if (threadIdx.x == 0) {
-    if (NF <= s.nf_max) b.flo[NF] = 0;  // so that the last partition ends at u = 2^32 - 1
-    b.tstart[NS] = ok ? (uint32_t)T : 0u;  // no tasks when a capacity is exceeded
-    meta->n_fine = ok ? NF : 0;                 // later kernels never index past nf_max
-    meta->n_tasks = ok ? T : 0;
-    if (!ok) atomicOr(&meta->status, ST_INTERNAL);
+    if (NF <= nf_max) flo[NF] = 0;  // so that the last partition ends at u = 2^32 - 1
+    fine_base[P1] = (uint32_t)NF;
+    meta->n_fine = NF <= nf_max ? NF : 0;  // later kernels never index past nf_max
+    if (NF > nf_max) atomicOr(&meta->status, ST_INTERNAL);
   }
 }
-__global__ void k_fine_plan(Shape s, Buffers b) { fine_plan_body(s, b); }
+__global__ void k_fine_plan(const uint64_t* cstart, const uint32_t* hll, uint32_t* fine_base, uint32_t* fine_m,
+                            uint32_t* flo, int P1, int b1, uint32_t fine_target, uint32_t nf_max, Meta* meta) {
+  fine_plan_body(cstart, hll, fine_base, fine_m, flo, P1, b1, fine_target, nf_max, meta);
+}
 __global__ void k_fine_plan_batch(BatchTab t) {
   KC_BATCH_PROLOGUE(t);
-  fine_plan_body(d.s, d.b);
+  fine_plan_body(d.b.cstart, d.b.hll, d.b.fine_base, d.b.fine_m, d.b.flo, 1 << d.s.b1, d.s.b1, d.s.fine_target,
+                 (uint32_t)d.s.nf_max, d.b.meta);
 }
 
 // ------------------------------------------------------------------ pass B
@@ -912,9 +883,7 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
         const bool v = (valid >> i) & 1u;
         if (v) {
           if constexpr (DIRECT) {
-            // the cursors of this variant are the first P1 words of toff (tile 0's offsets,
-            // which it does not read)
-            const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long*>(&b.toff[c]), 1ull);
+            const unsigned long long pos = atomicAdd(&b.fcur[c], 1ull);
             if (pos < s.cap) store_key(b.kbuf, pos, keys[i]);
             else atomicOr(&b.meta->status, ST_INTERNAL);
           } else {
@@ -990,15 +959,343 @@ __global__ void __launch_bounds__(NT, 2) k_scatter_batch(BatchTab t) {
   scatter_body<KW, NT, KEEP_C>(d.s, d.b, bid);
 }
 
+// ------------------------------------------------------------------ phase 2: fine split
+// Fine partition of a key: the coarse field c of u selects {first fine partition of c,
+// m_c}; the fine index is floor(v m_c / 2^(32 - b1)) for the low part v of u (below the
+// coarse field), taken as the high word of (v << b1) * m_c.  The m_c fine partitions of c
+// split its range of u into near-equal parts.
+struct FineMap {
+  int k, canonical, b1;
+};
 
-// ------------------------------------------------------------------ phase 2: count helpers
+template <class K>
+__device__ __forceinline__ uint32_t fine_of(K key, const FineMap& x, const uint2* fmap) {
+  const uint32_t u = umap(top32_of(key, x.k), x.canonical);
+  const uint2 e = fmap[coarse_field(u, x.b1)];
+  return e.x + __umulhi(u << x.b1, e.y);
+}
+
+// fmap[c] = {fine_base[c], fine_m[c]} for c < P1, fmap[P1].x = fine partition count.
+__device__ __forceinline__ void load_fine_map(const Buffers& b, int P1, uint2* fmap) {
+  for (int c = threadIdx.x; c <= P1; c += blockDim.x) fmap[c] = make_uint2(b.fine_base[c], c < P1 ? b.fine_m[c] : 0u);
+}
+__host__ __device__ inline FineMap make_fine_map(const Shape& s) { return FineMap{s.k, s.canonical, s.b1}; }
+
+constexpr int kFineThreads = 512;
+constexpr int kFinePer = 8;  // keys per thread per chunk (loaded as 16-byte pairs / single u128, all before use)
+constexpr int kFineChunk = kFineThreads * kFinePer;
+
+// Load this thread's keys of the chunk [c0, c1): pairs of words (read-only path, all
+// loads issued before any use).  Key m of the thread is chunk key  (m / P) * P * T +
+// threadIdx.x * P + m % P, P = 16 / (8 KW) keys per load, T = threads.
+template <int KW>
+__device__ __forceinline__ void load_chunk(const uint64_t* __restrict__ src, uint64_t c0, uint64_t c1,
+                                           typename KeyT<KW>::T (&keys)[kFinePer], uint32_t& have) {
+  typedef typename KeyT<KW>::T K;
+  constexpr int P = KW == 1 ? 2 : 1;  // keys per 16-byte load
+  have = 0;
+  ulonglong2 v[kFinePer / P];
+#pragma unroll
+  for (int m = 0; m < kFinePer / P; ++m) {
+    const uint64_t i = c0 + (uint64_t)m * P * kFineThreads + (uint64_t)threadIdx.x * P;
+    v[m] = make_ulonglong2(0, 0);
+    if (i + P <= c1) v[m] = __ldg(reinterpret_cast<const ulonglong2*>(src + i * KW));
+    else if (i < c1) v[m].x = __ldg(src + i * KW);  // P == 2 and one key left
+  }
+#pragma unroll
+  for (int m = 0; m < kFinePer / P; ++m) {
+    const uint64_t i = c0 + (uint64_t)m * P * kFineThreads + (uint64_t)threadIdx.x * P;
+    if constexpr (KW == 1) {
+      keys[2 * m] = (K)v[m].x;
+      keys[2 * m + 1] = (K)v[m].y;
+      if (i < c1) have |= 1u << (2 * m);
+      if (i + 1 < c1) have |= 1u << (2 * m + 1);
+    } else {
+      keys[m] = (K)(((u128)v[m].y << 64) | v[m].x);
+      if (i < c1) have |= 1u << m;
+    }
+  }
+}
+
+// Chunks of the coarse-grouped keys are handed out round-robin.  A chunk's first and last
+// keys bound the fine partitions it touches; they are fetched for the block's next chunk
+// (cp.async into bnd_s[1 - cur]) while the current one is processed.
+template <int KW>
+__device__ __forceinline__ void fetch_bounds(const uint64_t* kbuf, uint64_t c0, uint64_t K_total,
+                                             typename KeyT<KW>::T* bnd) {
+  const uint64_t c1 = min(K_total, c0 + kFineChunk);
+  if constexpr (KW == 1) {
+    cp_async8(&bnd[0], kbuf + c0);
+    cp_async8(&bnd[1], kbuf + c1 - 1);
+  } else {
+    cp_async16(&bnd[0], kbuf + 2 * c0);
+    cp_async16(&bnd[1], kbuf + 2 * (c1 - 1));
+  }
+}
+
+template <int KW>
+__device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
+  typedef typename KeyT<KW>::T K;
+  extern __shared__ __align__(16) uint8_t sm[];
+  const int P1 = 1 << s.b1;
+  uint2* fmap = reinterpret_cast<uint2*>(sm);                    // [P1 + 1]
+  uint32_t* lh = reinterpret_cast<uint32_t*>(fmap + P1 + 1);     // [kFineLocalCap]
+  __shared__ __align__(16) K bnd_s[2][2];
+  load_fine_map(b, P1, fmap);
+  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
+  const FineMap x = make_fine_map(s);
+  const uint64_t K_total = min(b.meta->n_windows, s.cap);
+  const uint64_t stride = (uint64_t)nblk * kFineChunk;
+  if (threadIdx.x == 0 && bid * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, bid * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  int cur = 0;
+  for (uint64_t c0 = bid * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
+    const uint64_t c1 = min(K_total, c0 + kFineChunk);
+    const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
+    const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
+    if (threadIdx.x == 0 && c0 + stride < K_total) fetch_bounds<KW>(b.kbuf, c0 + stride, K_total, bnd_s[cur ^ 1]);
+    const bool local = span <= (uint32_t)kFineLocalCap;
+    K keys[kFinePer];
+    uint32_t have;
+    load_chunk<KW>(b.kbuf, c0, c1, keys, have);
+#pragma unroll
+    for (int m = 0; m < kFinePer; ++m) {
+      if ((have >> m) & 1u) {
+        const uint32_t g = fine_of(keys[m], x, fmap);
+        if (local && g - g_lo < span) atomicAdd(&lh[g - g_lo], 1u);
+        else if (g < s.nf_max) atomicAdd(&b.fhist[g], 1u);
+        else atomicOr(&b.meta->status, ST_INTERNAL);
+      }
+    }
+    __syncthreads();
+    if (local) {
+      for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
+        const uint32_t v = lh[i];
+        if (v) {
+          if (g_lo + i < s.nf_max) atomicAdd(&b.fhist[g_lo + i], v);
+          else atomicOr(&b.meta->status, ST_INTERNAL);
+          lh[i] = 0;
+        }
+      }
+    }
+    if (threadIdx.x == 0) cp_async_wait_all();
+    __syncthreads();
+  }
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b) {
+  fine_hist_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_hist_body<KW>(d.s, d.b, bid, nblk);
+}
+
+// Exclusive scan of the fine histogram (one block of 1024 threads).
+__device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b) {
+  __shared__ uint64_t wt[32];
+  __shared__ uint64_t carry_s;
+  const uint64_t NF = min(b.meta->n_fine, sh.nf_max);
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) carry_s = 0;
+  __syncthreads();
+  for (uint64_t base = 0; base < NF; base += (uint64_t)nt * 8) {
+    uint64_t v[8];
+    uint64_t s = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint64_t i = base + (uint64_t)t * 8 + m;
+      v[m] = i < NF ? b.fhist[i] : 0;
+      s += v[m];
+    }
+    uint64_t x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t w = wt[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += y;
+      }
+      wt[lane] = w;
+    }
+    __syncthreads();
+    uint64_t run = carry_s + x - s + (wid ? wt[wid - 1] : 0);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint64_t i = base + (uint64_t)t * 8 + m;
+      if (i < NF) {
+        b.foff[i] = run;
+        b.fcur[i] = run;
+      }
+      run += v[m];
+    }
+    __syncthreads();
+    if (t == 0) carry_s += wt[31];
+    __syncthreads();
+  }
+  if (t == 0) b.foff[NF] = carry_s;
+}
+__global__ void k_fine_scan(Shape sh, Buffers b) { fine_scan_body(sh, b); }
+__global__ void k_fine_scan_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_scan_body(d.s, d.b);
+}
+
+// Exclusive scan of in[0, n) into out[0, n) (all threads of the block, n <= 4 * blockDim);
+// returns the total.
+__device__ uint32_t block_scan_to(const uint32_t* in, uint32_t* out, int n, uint32_t* warp_tmp) {
+  const int nt = blockDim.x, t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = (nt + 31) >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  uint32_t x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < nw ? warp_tmp[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) warp_tmp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (wid ? warp_tmp[wid - 1] : 0);
+  const uint32_t total = warp_tmp[nw - 1];
+  for (int i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  __syncthreads();
+  return total;
+}
+
+// Split each chunk by fine partition: rank the keys in a shared histogram, bump each fine
+// partition's global cursor once per chunk, stage the keys grouped by fine partition and
+// write every group as one contiguous run.
+template <int KW>
+__device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
+  typedef typename KeyT<KW>::T K;
+  extern __shared__ __align__(16) uint8_t sm[];
+  const int P1 = 1 << s.b1;
+  K* stage = reinterpret_cast<K*>(sm);                                          // [kFineChunk]
+  uint16_t* stage_g = reinterpret_cast<uint16_t*>(stage + kFineChunk);          // [kFineChunk]
+  uint64_t* delta = reinterpret_cast<uint64_t*>(stage_g + kFineChunk);          // [kFineLocalCap]
+  uint32_t* lh = reinterpret_cast<uint32_t*>(delta + kFineLocalCap);            // [kFineLocalCap]
+  uint32_t* soff = lh + kFineLocalCap;                                          // [kFineLocalCap]
+  uint2* fmap = reinterpret_cast<uint2*>(soff + kFineLocalCap);                 // [P1 + 1]
+  __shared__ __align__(16) K bnd_s[2][2];
+  __shared__ uint32_t wt[32];
+  load_fine_map(b, P1, fmap);
+  for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
+  const FineMap x = make_fine_map(s);
+  const uint64_t K_total = min(b.meta->n_windows, s.cap);
+  const uint64_t stride = (uint64_t)nblk * kFineChunk;
+  if (threadIdx.x == 0 && bid * (uint64_t)kFineChunk < K_total) {
+    fetch_bounds<KW>(b.kbuf, bid * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  int cur = 0;
+  for (uint64_t c0 = bid * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
+    const uint64_t c1 = min(K_total, c0 + kFineChunk);
+    const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
+    const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
+    if (threadIdx.x == 0 && c0 + stride < K_total) fetch_bounds<KW>(b.kbuf, c0 + stride, K_total, bnd_s[cur ^ 1]);
+    if (span == 0 || span > (uint32_t)kFineLocalCap) {
+      // a chunk over very many tiny fine partitions: one global cursor bump per key
+      for (int m = 0; m < kFinePer; ++m) {
+        const uint64_t i = c0 + threadIdx.x + (uint64_t)m * kFineThreads;
+        if (i < c1) {
+          K key;
+          load_key(b.kbuf, i, key);
+          const uint32_t g = fine_of(key, x, fmap);
+          const uint64_t pos = g < s.nf_max ? atomicAdd(&b.fcur[g], 1ull) : ~0ull;
+          if (pos < s.cap) store_key(b.sbuf, pos, key);
+          else atomicOr(&b.meta->status, ST_INTERNAL);
+        }
+      }
+    } else {
+      K keys[kFinePer];
+      uint32_t gr[kFinePer];
+      uint32_t have;
+      load_chunk<KW>(b.kbuf, c0, c1, keys, have);
+#pragma unroll
+      for (int m = 0; m < kFinePer; ++m) {
+        gr[m] = 0xffffffffu;
+        if ((have >> m) & 1u) {
+          const uint32_t lg = fine_of(keys[m], x, fmap) - g_lo;
+          if (lg < span) gr[m] = (lg << 16) | atomicAdd(&lh[lg], 1u);  // span <= 2^10, rank < 2^16
+          else atomicOr(&b.meta->status, ST_INTERNAL);
+        }
+      }
+      __syncthreads();
+      const uint32_t n_staged = block_scan_to(lh, soff, (int)span, wt);
+      // one cursor bump per fine partition; delta[lg] + staged position = global position
+      for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
+        const uint32_t v = lh[i];
+        if (v) {
+          uint64_t gb = s.cap;  // positions at or past cap are rejected below
+          if (g_lo + i < s.nf_max) gb = atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v);
+          else atomicOr(&b.meta->status, ST_INTERNAL);
+          delta[i] = gb - soff[i];
+          lh[i] = 0;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < kFinePer; ++m) {
+        if (gr[m] != 0xffffffffu) {
+          const uint32_t lg = gr[m] >> 16;
+          const uint32_t pos = soff[lg] + (gr[m] & 0xffffu);
+          stage[pos] = keys[m];
+          stage_g[pos] = (uint16_t)lg;
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < n_staged; i += kFineThreads) {
+        const uint64_t pos = delta[stage_g[i]] + i;
+        if (pos < s.cap) store_key(b.sbuf, pos, stage[i]);
+        else atomicOr(&b.meta->status, ST_INTERNAL);
+      }
+    }
+    if (threadIdx.x == 0) cp_async_wait_all();
+    __syncthreads();
+  }
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b) {
+  fine_scatter_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  fine_scatter_body<KW>(d.s, d.b, bid, nblk);
+}
+
+// ------------------------------------------------------------------ phase 2: count + emit
 constexpr uint64_t kLookValue = (1ull << 62) - 1;
 constexpr uint64_t kLookAgg = 1ull << 62;
 constexpr uint64_t kLookIncl = 2ull << 62;
 
 // Decoupled look-back (executed by one warp): sum of distinct counts of fine partitions < g.
-// (A decoupled look-back is the published single-pass prefix-scan method: each partition
-// publishes its own total as soon as it is known and its inclusive prefix once that is.)
 // Each step reads the kLookPer * 32 status words before position j at once (lane l holds
 // distance q * 32 + l); the nearest inclusive prefix among them ends the walk, and only
 // unpublished words nearer than it are waited for (with a bounded spin).  With `abort`,
@@ -1006,25 +1303,12 @@ constexpr uint64_t kLookIncl = 2ull << 62;
 constexpr int kLookPer = 8;
 constexpr uint64_t kNoPrefix = ~0ull;
 __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* status, uint32_t spin_limit,
-                             const volatile uint32_t* abort = nullptr, unsigned long long* prof = nullptr) {
+                             const volatile uint32_t* abort = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kNone = kLookPer * 32;
   uint64_t excl = 0;
   int64_t j = (int64_t)g - 1;
-  uint32_t steps = 0, waits = 0;
-  struct Tally {  // profiled calls: walk steps and wait iterations, added by lane 0 on return
-    unsigned long long* p;
-    const uint32_t &st, &wt;
-    int lane;
-    __device__ ~Tally() {
-      if (p && lane == 0) {
-        p[0] += st;
-        p[1] += wt;
-      }
-    }
-  } tally_{prof, steps, waits, lane};
   while (j >= 0) {
-    ++steps;
     uint64_t v[kLookPer];
 #pragma unroll
     for (int q = 0; q < kLookPer; ++q) {
@@ -1044,7 +1328,6 @@ __device__ uint64_t lookback(unsigned long long* look, uint64_t g, uint32_t* sta
       for (int q = 0; q < kLookPer; ++q) wait |= (uint32_t)(q * 32 + lane) < stop && (v[q] >> 62) == 0;
       if (!__any_sync(0xffffffffu, wait)) break;
       if (abort && *abort) return kNoPrefix;
-      ++waits;
       if (++spins > spin_limit) {
         if (lane == 0) atomicOr(status, ST_TIMEOUT);
         return excl;
@@ -1076,56 +1359,42 @@ struct Table {
   uint32_t* counts;
 };
 
-// Shared memory of the phase-2 kernel.  The count tasks use a hash table of 2^bT_max slots
-// (key + count), a bucket histogram of hist_max(kw) entries and the 16-bit slot numbers of
-// up to 3/4 of the slots in output order; the split tasks reuse the same bytes for their
-// staging (keys and their fine partitions) and four per-fine-partition arrays.  After it
-// come the areas every task keeps: the ticket layout (stage starts, count starts) and one
-// batch of a fine partition's runs.
-constexpr int kTableLog2Cap = 13;  // 8192 slots: 8 per thread of the 1024-thread block
-__host__ __device__ constexpr int hist_max(int kw) { return kw == 1 ? 16384 : 8192; }
-constexpr int kBinsPad = kMaxFine + 1 + ((kMaxFine + 1) >> 5) + 1;  // padded_len(kMaxFine + 1)
-__host__ __device__ inline size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
-__host__ __device__ inline size_t count_area_bytes(int kw, int bT_max) {
+// Count kernel shared memory: a hash table of 2^bT_max slots (key + count), a bucket
+// histogram of hist_max(kw) entries and the 16-bit slot numbers of up to 3/4 of the slots
+// in output order.
+constexpr int kTableLog2Cap = kCountThreads == 1024 ? 13 : 12;  // 8 slots per thread
+__host__ __device__ constexpr int hist_max(int kw) {
+  return kCountThreads == 1024 ? (kw == 1 ? 16384 : 8192) : 4096;
+}
+
+size_t count_kernel_smem(int kw, int bT_max, int /*unused*/) {
   const size_t slots = (size_t)1 << bT_max;
   return slots * (size_t)(kw * 8 + 4) + padded_len(hist_max(kw)) * 4 + ((3 * slots) >> 2) * 2 + 256;
 }
-__host__ __device__ inline size_t split_area_bytes(int kw) {
-  return (size_t)split_sub(kw) * (kw * 8 + 2) + 4 * (size_t)kBinsPad * 4;
-}
-__host__ __device__ inline size_t phase2_area(int kw, int bT_max) {
-  const size_t a = count_area_bytes(kw, bT_max), b = split_area_bytes(kw);
-  return align_to(a > b ? a : b, 16);
-}
-__host__ __device__ constexpr int max_coarse(int kw) { return 1 << max_coarse_log2(kw); }
-__host__ __device__ inline size_t persist_bytes(int kw) {
-  return (size_t)(2 * (max_coarse(kw) + kStageLag) + 1) * 4 + (size_t)(3 * kRunBatch + 1) * 4 + 16;
-}
-size_t phase2_smem(int kw, int bT_max) { return phase2_area(kw, bT_max) + persist_bytes(kw); }
 
-int table_log2_max(int kw, size_t smem_optin) {
+// The largest table whose block (8 KB of static shared memory included) fits the opt-in
+// limit, with kCountBlocksPerSM blocks on one SM (each also keeps 1 KB for the system).
+int table_log2_max(int kw, size_t smem_optin, size_t smem_per_sm) {
+  size_t budget = smem_optin;
+  if (kCountBlocksPerSM > 1 && smem_per_sm) {
+    const size_t per = smem_per_sm / kCountBlocksPerSM - 1024;
+    budget = per < budget ? per : budget;
+  }
   int best = 6;
   for (int bt = 6; bt <= kTableLog2Cap; ++bt)
-    if (phase2_smem(kw, bt) + 8192 <= smem_optin) best = bt;  // 8 KB for static shared memory
+    if (count_kernel_smem(kw, bt, 0) + 8192 <= budget) best = bt;
   return best;
-}
-
-// A deferred run in the stage: keys (dcap + 1 of them, the all-ones key included), then
-// counts, each part on whole 128-byte lines.
-__host__ __device__ inline size_t stage_keys_bytes(int kw, int bT_max) {
-  return align_to((((size_t)3 << bT_max) / 4 + 1) * kw * 8, 128);
-}
-size_t stage_slot_bytes(int kw, int bT_max) {
-  return align_to(stage_keys_bytes(kw, bT_max) + align_to((((size_t)3 << bT_max) / 4 + 1) * 4, 128), 256);
 }
 
 constexpr int kProbeLimit = 128;
 constexpr int kWorkers = kCountThreads - 32;  // warps 1.. load and sort while warp 0 looks back
 constexpr int kSlotsPerWorker = ((1 << kTableLog2Cap) + kWorkers - 1) / kWorkers;
 
-// counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes)
+// counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes).
+// 64-bit keys start their probe sequence at an even slot, so that its first two slots are
+// one aligned 16-byte pair that a single shared-memory load reads.
 __device__ __forceinline__ uint32_t hslot(uint64_t key, int bT) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bT));
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bT)) & ~1u;
 }
 __device__ __forceinline__ uint32_t hslot(u128 key, int bT) {
   const uint64_t h = ((uint64_t)key ^ ((uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
@@ -1151,7 +1420,7 @@ __device__ __forceinline__ void bar_workers() {
 // new slot, 1 if it was already there, 0 if no slot was found within the probe limit.
 template <int KW>
 __device__ __forceinline__ int count_insert(Table<KW> tb, typename KeyT<KW>::T key, uint32_t inc, int bT, bool check,
-                                            uint32_t* status) {
+                                            uint32_t limit, uint32_t* status) {
   typedef typename KeyT<KW>::T K;
   const K EMPTY = all_ones<K>();
   const uint32_t mask = (1u << bT) - 1;
@@ -1174,7 +1443,7 @@ __device__ __forceinline__ int count_insert(Table<KW> tb, typename KeyT<KW>::T k
     if (res) {
       if (check) {
         const uint32_t o = atomicAdd(&tb.counts[s], inc);
-        if (o > 0xffffffffu - inc) atomicOr(status, ST_COUNT_OVERFLOW);
+        if (o > limit - inc) atomicOr(status, ST_COUNT_OVERFLOW);
       } else {
         atomicAdd(&tb.counts[s], inc);  // result unused: a reduction
       }
@@ -1191,6 +1460,98 @@ __device__ __forceinline__ void table_clear(Table<KW> tb, uint32_t nslots) {
     tb.keys[i] = all_ones<K>();
     tb.counts[i] = 0;
   }
+}
+
+// Count the keys in[0, n) (only those in [lo, hi] when `ranged`).  The all-ones key is
+// counted apart in *special (it marks empty slots); it exists only when the k-mer fills
+// the key word (full_width).  Sets *ovf if a key found no slot.
+// With MERGE, a warp whose active keys are all equal adds them with one atomic (the
+// heavy-hitter merge of the paper's L3 layer); without it (the default) every key is added
+// on its own: on GB300 the shared-memory atomics absorb equal keys faster than the merge's
+// warp vote costs, even for a single key.
+template <int KW, bool MERGE = false>
+__device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ranged, typename KeyT<KW>::T lo,
+                          typename KeyT<KW>::T hi, int bT, bool full_width, uint32_t limit, uint32_t* n_new,
+                          uint32_t* ovf, uint32_t* special, uint32_t* status) {
+  typedef typename KeyT<KW>::T K;
+  constexpr int kIn = KW == 1 ? 8 : 2;  // loads in flight per thread (u128 keys: register-bound at 64)
+  const K EMPTY = all_ones<K>();
+  const int lane = threadIdx.x & 31;
+  const bool check = n > limit;  // a count can pass the limit only in a partition that large
+  uint32_t claimed = 0;
+  for (uint64_t base = 0; base < n; base += kIn * (uint64_t)blockDim.x) {
+    K kk[kIn];
+    bool aa[kIn];
+#pragma unroll
+    for (int m = 0; m < kIn; ++m) {
+      const uint64_t i = base + (uint64_t)m * blockDim.x + threadIdx.x;
+      kk[m] = 0;
+      aa[m] = i < n;
+      if (aa[m]) load_key(in, i, kk[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < kIn; ++m) {
+      const K key = kk[m];
+      bool act = aa[m];
+      if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
+      // a warp whose active keys all equal lane 0's key (a heavy hitter) adds them at once;
+      // lane 0's own key counts only if it is active, so any inactive lane 0 is harmless
+      const K k0 = shfl_key(key, 0);
+      if (MERGE && __all_sync(0xffffffffu, !act || key == k0)) {
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        if (am && lane == __ffs(am) - 1) {
+          const uint32_t inc = __popc(am);
+          if (full_width && k0 == EMPTY) {
+            if (atomicAdd(special, inc) > limit - inc) atomicOr(status, ST_COUNT_OVERFLOW);
+          } else {
+            const int r = count_insert<KW>(tb, k0, inc, bT, check, limit, status);
+            if (!r) atomicOr(ovf, 1u);
+            claimed += r == 2;
+          }
+        }
+      } else if (act) {
+        if (full_width && key == EMPTY) {
+          if (atomicAdd(special, 1u) >= limit) atomicOr(status, ST_COUNT_OVERFLOW);
+        } else {
+          int r = 0;
+          if constexpr (KW == 1) {
+            // the key's home pair, read at once: most keys are there already or claim a free
+            // slot of it; the others go on along the probe sequence
+            const uint32_t h = hslot(key, bT);
+            uint64_t* pk = reinterpret_cast<uint64_t*>(tb.keys);
+            const ulonglong2 v = ld_pair_shared(pk + h);
+            uint32_t sl = h;
+            if (v.x == (uint64_t)key) {
+              r = 1;
+            } else if (v.y == (uint64_t)key) {
+              r = 1;
+              sl = h + 1;
+            } else if (v.x == ~0ull || v.y == ~0ull) {
+              sl = v.x == ~0ull ? h : h + 1;
+              const unsigned long long old =
+                  atomicCAS(reinterpret_cast<unsigned long long*>(pk + sl), ~0ull, (unsigned long long)key);
+              r = old == ~0ull ? 2 : (old == (unsigned long long)key ? 1 : 0);
+            }
+            if (r) {
+              if (check) {
+                if (atomicAdd(&tb.counts[sl], 1u) >= limit) atomicOr(status, ST_COUNT_OVERFLOW);
+              } else {
+                atomicAdd(&tb.counts[sl], 1u);  // result unused: a reduction
+              }
+            }
+          }
+          if (!r) r = count_insert<KW>(tb, key, 1u, bT, check, limit, status);
+          if (!r) atomicOr(ovf, 1u);
+          claimed += r == 2;
+        }
+      }
+    }
+  }
+  // the slots claimed, added once per warp (a shared counter bumped per new key would be
+  // one address hit by every lane of a warp whose keys are all new)
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) claimed += __shfl_xor_sync(0xffffffffu, claimed, d);
+  if (lane == 0 && claimed) atomicAdd(n_new, claimed);
 }
 
 template <class K> __device__ __forceinline__ int bitlen(K v);
@@ -1261,7 +1622,9 @@ __device__ void warp_sort_idx(const K* keys, uint16_t* idx, uint32_t a, uint32_t
   }
 }
 
-constexpr int kRankPer = 7;           // positions per worker thread: 7 * 992 >= 3/4 of 8192 slots
+// positions per worker thread: 7 * 992 >= 3/4 of 8192 slots, 7 * 480 >= 3/4 of 4096
+constexpr int kRankPer = ((3 << kTableLog2Cap) / 4 + kWorkers - 1) / kWorkers;
+static_assert(kRankPer == 7, "rank registers sized for 7 positions per worker");
 constexpr int kRankRegs = (kRankPer + 1) / 2;  // ranks (< 2^13) are kept two per register
 __device__ __forceinline__ uint32_t rank_get(const uint32_t (&rk)[kRankRegs], int m) {
   return (rk[m >> 1] >> (16 * (m & 1))) & 0xffffu;
@@ -1448,903 +1811,386 @@ __device__ __forceinline__ void emit_slots(Table<KW> tb, const uint16_t* idx, ui
 
 __device__ __forceinline__ int ceil_log2_u32(uint32_t v) { return v <= 1 ? 0 : 32 - __clz(v - 1); }
 
-// ------------------------------------------------------------------ phase 2: split + count
-// One persistent kernel does the second phase for every coarse partition in turn.  Its
-// work is a list of tasks taken in ticket order, laid out stage by stage: stage s holds the
-// split tasks of coarse partition s, then the count tasks of coarse partition s - 1.
-//
-//   split task (c, j)   chunk j of coarse partition c (split_chunk keys of kbuf): the
-//                       chunk's fine-partition histogram, then its keys placed in sbuf at
-//                       the same positions, grouped by fine partition (staged per
-//                       sub-chunk in shared memory, written as runs); where each fine
-//                       partition's run starts in the chunk goes to rstart.
-//   count task (c, f)   fine partition g = fine_base[c] + f: waits until every split task
-//                       of c is done, gathers its run from every chunk of c, counts the
-//                       keys in a shared-memory table, orders the distinct keys and writes
-//                       them out (Algorithm 3 after its barrier: Sort + Accumulate).
-//
-// A coarse partition is small enough (about 19 MB of keys) that its chunks are still in
-// L2 when its count tasks read them one stage later, and the lines a count task has read
-// are discarded from L2 (discard.global.L2), so the split copy is not written back to HBM.
-// Every wait is on a task with a smaller ticket (tickets are taken in order by running
-// thread blocks), so the smallest unfinished ticket always makes progress.
-//
-// Output offsets come from a decoupled look-back over the fine partitions (the published
-// single-pass scan method: each partition publishes its total as soon as it is known and
-// its inclusive prefix once that is).  A partition whose prefix is not known when its keys
-// are ordered leaves its run in the block's own stage slot (in L2) and writes it out later,
-// once its prefix is known: when the block needs the slot again, after a later task if the
-// prefix is known by then without waiting, or at the end.
-
-__device__ __forceinline__ void discard_l2(uintptr_t line) {
-  asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
-}
-// Discard the 128-byte lines that lie wholly inside the bytes [lo, hi); thread i of n.
-__device__ __forceinline__ void discard_lines(const void* lo, const void* hi, uint32_t i, uint32_t n) {
-  const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, e = (uintptr_t)hi & ~(uintptr_t)127;
-  for (uintptr_t x = a + (uintptr_t)i * 128; x < e; x += (uintptr_t)n * 128) discard_l2(x);
-}
-__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-// Data written by other thread blocks of the same launch is read at L2 (ld.global.cg).
-__device__ __forceinline__ void load_key_cg(const uint64_t* src, uint64_t i, uint64_t& key) { key = __ldcg(src + i); }
-__device__ __forceinline__ void load_key_cg(const uint64_t* src, uint64_t i, u128& key) {
-  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(src) + i);
-  key = ((u128)v.y << 64) | v.x;
-}
-
-// Fine partition of a key inside its coarse partition (m parts of the coarse range of u):
-// floor(v m / 2^(32 - b1)) for the low part v of u, the high word of (v << b1) m.
-template <class K>
-__device__ __forceinline__ uint32_t fine_in_coarse(K key, int k, int canonical, int b1, uint32_t m, uint32_t& coarse) {
-  const uint32_t u = umap(top32_of(key, k), canonical);
-  coarse = coarse_field(u, b1);
-  return __umulhi(b1 ? u << b1 : u, m);
-}
-
-// Shared state of a phase-2 thread block that outlives one task.
-struct P2State {
-  // the next task, prepared by thread 0 while the block finishes the current one
-  uint64_t nx_cs, nx_ce, nx_tb, nx_g;
-  uint32_t nx_kind, nx_c, nx_i, nx_m, nx_ulo, nx_uhi;
-  // deferred runs waiting in this block's stage slots, oldest first: slot (pend_head + i) %
-  // n_slots holds partition pend_g[...] with pend_d[...] entries, for i < pend_n
-  uint64_t pend_g[kMaxSlots];
-  uint32_t pend_d[kMaxSlots];
-  uint32_t pend_head, pend_n;
-  uint64_t excl;
-  uint32_t ordered, one, ovf, special, nnew, wait_ok, big_n;
-  uint32_t nseg;
-  uint64_t nkeys;
-  int stk_n;
-  // profiled plans: thread 0's cycles per phase and task tallies (added to the status record)
-  unsigned long long acc[8], tally[8];
-  long long tmark;
-};
-enum : uint32_t { TASK_SPLIT = 0, TASK_COUNT = 1, TASK_DONE = 2 };
-
-template <int KW, bool MERGE>
-struct Phase2 {
-  typedef typename KeyT<KW>::T K;
-  static constexpr uint32_t SUB = split_sub(KW), CH = split_chunk(KW), PER = SUB / kCountThreads;
-  static constexpr int kIn = KW == 1 ? 8 : 2;  // keys in flight per lane while counting
-  const Shape& s;
-  const Buffers& b;
-  uint8_t* sm;
-  P2State& st;
-  uint32_t* wtmp;       // [32]
-  uint32_t* tstart_s;   // [P1 + 2]
-  uint32_t* tsplit_s;   // [P1 + 1]
-  uint32_t* run_st;     // [kRunBatch] start of each run inside its coarse partition
-  uint32_t* run_len;    // [kRunBatch]
-  uint32_t* run_pre;    // [kRunBatch + 1] exclusive prefix of the run lengths
-  K* red_lo;            // [32]
-  K* red_hi;            // [32]
-  K* range_s;           // [2]
-  K* stk_lo;            // [160]
-  K* stk_hi;            // [160]
-  uint32_t* big_s;      // [kBigMax]
-  uint8_t* slots;       // this block's stage slots
-  int P1;
-  uint32_t cap_slots, dcap;
-
-  __device__ uint32_t tid() const { return threadIdx.x; }
-  // profiled plans: the cycles since the last mark go to phase i (thread 0's view; it takes
-  // part in every block barrier, so its time is the block's)
-  __device__ void mark(int i) {
-    if (s.profile && tid() == 0) {
-      const long long now = clock64();
-      st.acc[i] += (unsigned long long)(now - st.tmark);
-      st.tmark = now;
-    }
-  }
-  __device__ void tally(int i, unsigned long long v = 1) {
-    if (s.profile && tid() == 0) st.tally[i] += v;
-  }
-
-  // ---- thread 0: take the next ticket and look its task up
-  __device__ void prefetch() {
-    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(&b.meta->ticket);
-    const uint64_t t = atomicAdd(ticket, 1ull);
-    const uint64_t n_tasks = tstart_s[P1 + kStageLag];
-    if (t >= n_tasks) {
-      st.nx_kind = TASK_DONE;
-      return;
-    }
-    int lo = 0, hi = P1 + kStageLag - 1;  // the stage: last s with tstart_s[s] <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (tstart_s[mid] <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    uint32_t c, i, kind;
-    if (t < tsplit_s[lo]) {
-      kind = TASK_SPLIT;
-      c = (uint32_t)lo;
-      i = (uint32_t)(t - tstart_s[lo]);
-    } else {
-      kind = TASK_COUNT;
-      c = (uint32_t)(lo - kStageLag);
-      i = (uint32_t)(t - tsplit_s[lo]);
-    }
-    st.nx_kind = kind;
-    st.nx_c = c;
-    st.nx_i = i;
-    st.nx_cs = b.cstart[c];
-    st.nx_ce = b.cstart[c + 1];
-    st.nx_m = b.fine_m[c];
-    st.nx_tb = b.tbase[c];
-    if (kind == TASK_COUNT) {
-      const uint64_t g = (uint64_t)b.fine_base[c] + i;
-      st.nx_g = g;
-      st.nx_ulo = b.flo[g];
-      st.nx_uhi = b.flo[g + 1] - 1u;  // flo[NF] = 0: the last interval ends at 2^32 - 1
-    }
-  }
-
-  // ---- split task (c, j)
-  // One warp's exclusive scan of the padded array d[0, n) in place (lane l takes a contiguous
-  // stretch); returns the total to every lane.
-  __device__ static uint32_t warp_scan_pad(uint32_t* d, uint32_t n) {
-    const uint32_t lane = threadIdx.x & 31, per = (n + 31) >> 5;
-    const uint32_t a = min(n, lane * per), e = min(n, a + per);
-    uint32_t sum = 0;
-    for (uint32_t i = a; i < e; ++i) sum += d[PAD(i)];
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= (uint32_t)o) x += y;
-    }
-    uint32_t run = x - sum;
-    for (uint32_t i = a; i < e; ++i) {
-      const uint32_t v = d[PAD(i)];
-      d[PAD(i)] = run;
-      run += v;
-    }
-    return __shfl_sync(0xffffffffu, x, 31);
-  }
-
-  __device__ void split(uint32_t c, uint32_t j, uint64_t cs, uint64_t ce, uint32_t m, uint64_t tb) {
-    K* stage = reinterpret_cast<K*>(sm);
-    uint16_t* stage_g = reinterpret_cast<uint16_t*>(stage + SUB);
-    uint32_t* cur = reinterpret_cast<uint32_t*>(stage_g + SUB);  // padded [m + 1]: counts, then cursors
-    uint32_t* scnt = cur + kBinsPad;                               // padded [m]: keys of the sub-chunk
-    uint32_t* soff = scnt + kBinsPad;                              // padded [m]: their staged start
-    int32_t* delta = reinterpret_cast<int32_t*>(soff + kBinsPad);  // [m]: chunk position - staged position
-    const uint32_t t = tid();
-    const uint64_t nc = ce - cs;
-    const uint64_t nch = (nc + CH - 1) / CH;
-    const uint64_t lo = cs + (uint64_t)j * CH, hi = min(lo + CH, ce);
-    const int k = s.k, can = s.canonical, b1 = s.b1;
-    bool bad = m == 0 || m > (uint32_t)kMaxFine;
-    if (bad) m = 1;
-    // pass 1: how many keys of the chunk each fine partition gets
-    for (uint32_t f = t; f <= m; f += kCountThreads) {
-      cur[PAD(f)] = 0;
-      scnt[PAD(f)] = 0;
-    }
-    block_sync();
-    for (uint64_t base = lo; base < hi; base += SUB) {
-      K keys[PER];
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        const uint64_t i = base + t + (uint64_t)q * kCountThreads;
-        keys[q] = 0;
-        if (i < hi) load_key(b.kbuf, i, keys[q]);
-      }
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        const uint64_t i = base + t + (uint64_t)q * kCountThreads;
-        if (i < hi) {
-          uint32_t cc;
-          const uint32_t f = fine_in_coarse(keys[q], k, can, b1, m, cc);
-          if (cc == c && f < m) atomicAdd(&cur[PAD(f)], 1u);
-          else bad = true;
-        }
-      }
-    }
-    block_sync();
-    if (t < 32) warp_scan_pad(cur, m + 1);  // cur[PAD(m)]: keys of the chunk
-    block_sync();
-    for (uint32_t f = t; f <= m; f += kCountThreads)
-      b.rstart[tb + (uint64_t)f * nch + j] = (uint16_t)cur[PAD(f)];  // < 2^16: a chunk holds at most 32768 keys
-    // pass 2: each sub-chunk's keys ranked by fine partition, staged and written as runs at
-    // their partition's place in the chunk.  Three barriers per sub-chunk: one warp scans
-    // the sub-chunk's counts (and advances the cursors, and clears the counts) between the
-    // ranking and the staging, and the write-out of a sub-chunk overlaps the ranking of
-    // the next.  Warp 0 does not write out: thread 0 takes the next ticket meanwhile.
-    for (uint64_t base = lo; base < hi; base += SUB) {
-      K keys[PER];
-      uint32_t fr[PER];
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        const uint64_t i = base + t + (uint64_t)q * kCountThreads;
-        keys[q] = 0;
-        if (i < hi) load_key(b.kbuf, i, keys[q]);
-      }
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        const uint64_t i = base + t + (uint64_t)q * kCountThreads;
-        fr[q] = 0xffffffffu;
-        if (i < hi) {
-          uint32_t cc;
-          const uint32_t f = fine_in_coarse(keys[q], k, can, b1, m, cc);
-          if (cc == c && f < m) fr[q] = (f << 16) | atomicAdd(&scnt[PAD(f)], 1u);  // rank < SUB <= 2^13
-          else bad = true;
-        }
-      }
-      block_sync();  // ranks taken; the previous sub-chunk is written out
-      if (t < 32) {
-        const uint32_t lane = t;
-        const uint32_t per = (m + 31) >> 5;
-        const uint32_t a = min(m, lane * per), e = min(m, a + per);
-        uint32_t sum = 0;
-        for (uint32_t f = a; f < e; ++f) sum += scnt[PAD(f)];
-        uint32_t x = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= (uint32_t)o) x += y;
-        }
-        uint32_t run = x - sum;
-        for (uint32_t f = a; f < e; ++f) {
-          const uint32_t v = scnt[PAD(f)];
-          soff[PAD(f)] = run;
-          delta[f] = (int32_t)cur[PAD(f)] - (int32_t)run;
-          cur[PAD(f)] += v;
-          scnt[PAD(f)] = 0;
-          run += v;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
-        if (lane == 0) st.nseg = tot;  // keys staged in this sub-chunk
-      }
-      block_sync();
-      const uint32_t n_staged = min((uint32_t)umin64(SUB, hi - base), st.nseg);
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        if (fr[q] != 0xffffffffu) {
-          const uint32_t f = fr[q] >> 16;
-          const uint32_t pos = soff[PAD(f)] + (fr[q] & 0xffffu);
-          if (pos < n_staged) {
-            stage[pos] = keys[q];
-            stage_g[pos] = (uint16_t)f;
-          } else {
-            bad = true;
-          }
-        }
-      }
-      block_sync();
-      if (base + SUB >= hi && t == 0) prefetch();
-      if (t >= 32) {
-        for (uint32_t i = t - 32; i < n_staged; i += kCountThreads - 32) {
-          const uint64_t dst = (uint64_t)((int64_t)lo + delta[stage_g[i]] + (int64_t)i);
-          if (dst >= lo && dst < hi) store_key(b.sbuf, dst, stage[i]);
-          else bad = true;
-        }
-      }
-    }
-    if (lo >= hi && t == 0) prefetch();  // an empty chunk (cannot happen: chunks cover the keys)
-    // the chunk's keys in kbuf are not read again
-    discard_lines(b.kbuf + lo * KW, b.kbuf + hi * KW, t, kCountThreads);
-    if (bad) atomicOr(&b.meta->status, ST_INTERNAL);
-    block_sync();
-    if (t == 0) {
-      __threadfence();
-      atomicAdd(&b.sdone[c], 1u);
-    }
-    mark(0);
-    tally(0);
-  }
-
-  // ---- count task: the runs of fine partition f in the chunks [jb, jb + kRunBatch) of
-  // coarse partition c into run_st / run_len / run_pre; returns their keys (all threads)
-  __device__ uint64_t load_runs(uint64_t tb, uint32_t f, uint64_t nch, uint64_t jb, uint64_t nc) {
-    const uint32_t t = tid();
-    const uint64_t nr = umin64(kRunBatch, nch - jb);
-    uint32_t mine = 0;
-    for (uint32_t r = t; r < (uint32_t)kRunBatch; r += kCountThreads) {
-      uint32_t len = 0;
-      if (r < nr) {
-        const uint64_t jj = jb + r;
-        const uint32_t a = __ldcg(b.rstart + tb + (uint64_t)f * nch + jj);
-        const uint32_t e = __ldcg(b.rstart + tb + (uint64_t)(f + 1) * nch + jj);
-        // a run lies inside its chunk, and the chunk inside the coarse partition
-        if (e < a || jj * CH + e > nc) atomicOr(&b.meta->status, ST_INTERNAL);
-        else len = e - a;
-        run_st[r] = (uint32_t)(jj * CH) + a;
-        run_len[r] = len;
-      }
-      run_pre[r] = len;
-    }
-    block_sync();
-    const uint32_t total = block_exclusive_scan<uint32_t>(run_pre, kRunBatch, wtmp);
-    if (t == 0) run_pre[kRunBatch] = total;
-    block_sync();
-    return total;
-  }
-
-  // all keys of fine partition f (a pass over its run starts only)
-  __device__ uint64_t input_size(uint64_t tb, uint32_t f, uint64_t nch, uint64_t nc) {
-    const uint32_t t = tid();
-    uint64_t mine = 0;
-    for (uint64_t jj = t; jj < nch; jj += kCountThreads) {
-      const uint32_t a = __ldcg(b.rstart + tb + (uint64_t)f * nch + jj);
-      const uint32_t e = __ldcg(b.rstart + tb + (uint64_t)(f + 1) * nch + jj);
-      if (e >= a && jj * CH + e <= nc) mine += e - a;
-    }
-    if (t == 0) st.nkeys = 0;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
-    block_sync();
-    if ((t & 31) == 0 && mine) atomicAdd(reinterpret_cast<unsigned long long*>(&st.nkeys), (unsigned long long)mine);
-    block_sync();
-    return st.nkeys;
-  }
-
-  // Count the keys of the loaded runs (only those in [lo, hi] when `ranged`).  The runs are
-  // read as one sequence (run_pre: where each starts in it) in chunks of 256 keys, warp w
-  // taking chunks w, w + 32, ...; each lane finds its key's run by stepping forward from
-  // the chunk's first run.  The all-ones key is counted apart in st.special (it marks empty
-  // slots); it exists only when the k-mer fills the key word (full_width).  With MERGE, a
-  // warp whose active keys are all equal adds them with one atomic (the heavy-hitter merge
-  // of the paper's L3 layer).  Returns the slots this thread claimed.
-  __device__ uint32_t count_runs(Table<KW> tb, const uint64_t* src, uint32_t nr, bool ranged, K lo, K hi, int bT,
-                                 bool full_width, bool check) {
-    const K EMPTY = all_ones<K>();
-    const uint32_t lane = tid() & 31, w = tid() >> 5;
-    const uint32_t n = nr ? run_pre[kRunBatch] : 0;
-    uint32_t claimed = 0;
-    for (uint32_t base = w * 256; base < n; base += (kCountThreads / 32) * 256) {
-      int a = 0, z = (int)nr - 1;  // the run of key `base`: last r with run_pre[r] <= base
-      while (a < z) {
-        const int mid = (a + z + 1) >> 1;
-        if (run_pre[mid] <= base) a = mid;
-        else z = mid - 1;
-      }
-      uint32_t r = (uint32_t)a;
-      for (uint32_t m0 = 0; m0 < 256; m0 += 32 * kIn) {
-        K kk[kIn];
-        bool aa[kIn];
-#pragma unroll
-        for (int m = 0; m < kIn; ++m) {
-          const uint32_t i = base + m0 + lane + 32 * m;
-          kk[m] = 0;
-          aa[m] = i < n;
-          if (aa[m]) {
-            while (r + 1 < nr && run_pre[r + 1] <= i) ++r;
-            load_key_cg(src, (uint64_t)run_st[r] + (i - run_pre[r]), kk[m]);
-          }
-        }
-#pragma unroll
-        for (int m = 0; m < kIn; ++m) {
-          const K key = kk[m];
-          bool act = aa[m];
-          if (ranged) act = act && key >= lo && key <= hi && key != EMPTY;
-          const K k0 = shfl_key(key, 0);
-          if (MERGE && __all_sync(0xffffffffu, !act || key == k0)) {
-            const unsigned am = __ballot_sync(0xffffffffu, act);
-            if (am && lane == (uint32_t)(__ffs(am) - 1)) {
-              const uint32_t inc = __popc(am);
-              if (full_width && k0 == EMPTY) {
-                if (atomicAdd(&st.special, inc) > 0xffffffffu - inc) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
-              } else {
-                const int res = count_insert<KW>(tb, k0, inc, bT, check, &b.meta->status);
-                if (!res) atomicOr(&st.ovf, 1u);
-                claimed += res == 2;
-              }
-            }
-          } else if (act) {
-            if (full_width && key == EMPTY) {
-              if (atomicAdd(&st.special, 1u) == 0xffffffffu) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
-            } else {
-              const int res = count_insert<KW>(tb, key, 1u, bT, check, &b.meta->status);
-              if (!res) atomicOr(&st.ovf, 1u);
-              claimed += res == 2;
-            }
-          }
-        }
-      }
-    }
-    return claimed;
-  }
-
-  // Block-wide sum of the slots claimed into st.nnew (all threads).
-  __device__ void add_claimed(uint32_t claimed) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) claimed += __shfl_xor_sync(0xffffffffu, claimed, d);
-    if ((tid() & 31) == 0 && claimed) atomicAdd(&st.nnew, claimed);
-  }
-
-  // Discard the sbuf lines of the loaded runs (read for the last time).
-  __device__ void discard_runs(const uint64_t* src, uint32_t nr) {
-    const uint32_t lane = tid() & 31, w = tid() >> 5;
-    for (uint32_t r = w; r < nr; r += kCountThreads / 32)
-      discard_lines(src + (uint64_t)run_st[r] * KW, src + ((uint64_t)run_st[r] + run_len[r]) * KW, lane, 32);
-  }
-
-  __device__ uint8_t* slot_at(uint32_t i) const { return slots + (size_t)i * s.stage_bytes; }
-
-  // ---- the oldest run waiting in the stage: written out once its prefix is known.  With
-  // `blocking`, the look-back waits (bounded) for it; otherwise the call gives up at the
-  // first wait.  Returns whether it was written out (all threads).
-  __device__ bool finalize(bool blocking) {
-    block_sync();
-    if (st.pend_n == 0) return false;
-    const uint32_t si = st.pend_head;
-    const uint64_t g = st.pend_g[si];
-    const uint32_t d = st.pend_d[si];
-    const long long t0 = clock64();
-    if (tid() < 32) {
-      const uint64_t ex = lookback(b.look, g, &b.meta->status, s.spin_limit, blocking ? nullptr : &st.one,
-                                   s.profile && blocking ? &st.tally[6] : nullptr);
-      if (tid() == 0) st.excl = ex;
-    }
-    block_sync();
-    if (blocking) tally(4, (unsigned long long)(clock64() - t0));
-    const uint64_t ex = st.excl;
-    if (ex == kNoPrefix) return false;
-    uint8_t* slot = slot_at(si);
-    const uint64_t* skeys = reinterpret_cast<const uint64_t*>(slot);
-    const uint32_t* scnts = reinterpret_cast<const uint32_t*>(slot + stage_keys_bytes(KW, s.bT_max));
-    if (tid() == 0) st_status(&b.look[g], kLookIncl | (ex + d));
-    if (ex + d > s.cap) {
-      if (tid() == 0) atomicOr(&b.meta->status, ST_INTERNAL);
-    } else {
-      for (uint32_t i = tid(); i < d; i += kCountThreads) {
-        K key;
-        load_key_cg(skeys, i, key);
-        store_key(b.out_keys, ex + i, key);
-        b.out_counts[ex + i] = __ldcg(scnts + i);
-      }
-    }
-    block_sync();
-    // the slot is this block's own: its used lines are dropped without a write-back
-    discard_lines(slot, slot + align_to((size_t)d * KW * 8, 128), tid(), kCountThreads);
-    discard_lines(scnts, reinterpret_cast<const uint8_t*>(scnts) + align_to((size_t)d * 4, 128), tid(), kCountThreads);
-    if (tid() == 0) {
-      st.pend_head = (si + 1) % s.n_slots;
-      --st.pend_n;
-    }
-    block_sync();
-    return true;
-  }
-
-  // ---- count task (c, f)
-  __device__ void count(uint32_t c, uint32_t f, uint64_t g, uint64_t cs, uint64_t ce, uint64_t tb, uint32_t ulo,
-                        uint32_t uhi) {
-    const K EMPTY = all_ones<K>();
-    const uint32_t t = tid(), lane = t & 31, wid = t >> 5;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(sm + (size_t)cap_slots * (KW * 8 + 4));
-    uint16_t* idx = reinterpret_cast<uint16_t*>(hist + padded_len(hist_max(KW)));  // [dcap]
-    const uint64_t nch = (ce - cs + CH - 1) / CH;
-    const uint64_t* src = b.sbuf + cs * KW;
-    const bool full_width = s.k == 32 * KW;
-    if (t == 0) {
-      st.ovf = 0;
-      st.special = 0;
-      st.nnew = 0;
-      // the split of coarse partition c must be complete (bounded wait)
-      uint32_t spins = 0, ok = 1;
-      while (ld_acquire_u32(&b.sdone[c]) < (uint32_t)nch) {
-        if (++spins > kLookbackSpinLimit) {
-          atomicOr(&b.meta->status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-      st.wait_ok = ok;
-      if (spins) tally(2);
-    }
-    tally(1);
-    block_sync();
-    mark(1);
-    const uint64_t nch_eff = st.wait_ok ? nch : 0;
-    const bool one_batch = nch_eff <= (uint64_t)kRunBatch;
-    const uint64_t nc = ce - cs;
-    uint64_t n = one_batch ? load_runs(tb, f, nch_eff, 0, nc) : input_size(tb, f, nch_eff, nc);
-    uint32_t nr = (uint32_t)umin64(kRunBatch, nch_eff);
-    if (n > s.cap) {
-      if (t == 0) atomicOr(&b.meta->status, ST_INTERNAL);
-      n = 0;
-      nr = 0;
-      if (t == 0) run_pre[kRunBatch] = 0;
-    }
-    const bool check = n > 0xffffffffull;  // a count can pass 2^32 - 1 only in a partition that large
-    // table: at least twice the keys (at most that many distinct), within the cap
-    int bT = 6;
-    while (bT < s.bT_max && ((uint64_t)1 << bT) < 2 * n) ++bT;
-    Table<KW> tb_;
-    tb_.keys = reinterpret_cast<K*>(sm);
-    tb_.counts = reinterpret_cast<uint32_t*>(tb_.keys + (1u << bT));
-    table_clear<KW>(tb_, 1u << bT);
-    block_sync();
-    {
-      uint32_t claimed = 0;
-      if (one_batch) {
-        claimed = count_runs(tb_, src, nr, false, K(0), K(0), bT, full_width, check);
-      } else {
-        for (uint64_t jb = 0; jb < nch_eff; jb += kRunBatch) {
-          load_runs(tb, f, nch_eff, jb, nc);
-          claimed += count_runs(tb_, src, (uint32_t)umin64(kRunBatch, nch_eff - jb), false, K(0), K(0), bT,
-                                full_width, check);
-          block_sync();
-        }
-      }
-      add_claimed(claimed);
-    }
-    block_sync();
-    mark(2);
-    const uint32_t dn = st.nnew;
-    if (!st.ovf && dn <= dcap) {
-      if (one_batch) discard_runs(src, nr);
-      const uint64_t d = (uint64_t)dn + (st.special ? 1 : 0);
-      const bool publish = !(s.withhold && g == 0);
-      if (t == 0) {
-        if (publish) st_status(&b.look[g], (g == 0 && !s.defer_all ? kLookIncl : kLookAgg) | d);
-        b.fhist[g] = (uint32_t)d;
-        st.ordered = 0;
-      }
-      block_sync();
-      // Warp 0 resolves the exclusive prefix (look-back) while the workers order the table,
-      // waiting on unpublished predecessors only as long as the workers are busy.
-      uint32_t rank[kRankRegs];
-      if (wid == 0) {
-        const uint64_t ex =
-            s.defer_all ? kNoPrefix : g == 0 ? 0 : lookback(b.look, g, &b.meta->status, s.spin_limit, &st.ordered);
-        if (lane == 0) {
-          if (ex != kNoPrefix && g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
-          st.excl = ex;
-        }
-      } else {
-        if (t == 32) {
-          // every key of the partition lies in the key range of its range-map interval
-          uint32_t xlo, xhi;
-          x_range(ulo, uhi, s.canonical, xlo, xhi);
-          key_range(xlo, xhi, s.k, range_s[0], range_s[1]);
-        }
-        K klo;
-        int sh;
-        uint32_t NB;
-        bucket_slots<KW>(tb_, 1u << bT, dn, range_s, hist, idx, wtmp, big_s, &st.big_n, klo, sh, NB, &b.meta->status);
-        rank_slots<KW>(tb_, idx, idx, dn, hist, NB, klo, sh, big_s, st.big_n, rank, nullptr);
-        bar_workers();
-        if (t == 32) st.ordered = 1;
-      }
-      block_sync();
-      mark(3);
-      const uint64_t ex = st.excl;
-      if (ex != kNoPrefix) {
-        // direct: final positions; thread 0 takes the next ticket meanwhile
-        if (t == 0) prefetch();
-        if (wid > 0) emit_slots<KW>(tb_, idx, dn, rank, ex, b.out_keys, b.out_counts, s.cap, &b.meta->status);
-        if (t == 32 && st.special) {
-          if (ex + dn < s.cap) {
-            store_key(b.out_keys, ex + dn, EMPTY);
-            b.out_counts[ex + dn] = st.special;
-          } else {
-            atomicOr(&b.meta->status, ST_INTERNAL);
-          }
-        }
-        block_sync();
-        mark(4);
-        tally(3);
-      } else {
-        // deferred: the run waits in a stage slot of this block; when all are taken, the
-        // oldest is written out first (waiting for its prefix)
-        while (!finalize(false) && st.pend_n == s.n_slots) finalize(true);
-        if (t == 0) prefetch();
-        const uint32_t si = (st.pend_head + st.pend_n) % s.n_slots;
-        uint8_t* slot = slot_at(si);
-        uint64_t* okeys = reinterpret_cast<uint64_t*>(slot);
-        uint32_t* ocnts = reinterpret_cast<uint32_t*>(slot + stage_keys_bytes(KW, s.bT_max));
-        if (wid > 0) emit_slots<KW>(tb_, idx, dn, rank, 0, okeys, ocnts, (uint64_t)dcap + 1, &b.meta->status);
-        block_sync();
-        if (t == 32) {
-          if (st.special) {
-            store_key(okeys, dn, EMPTY);
-            ocnts[dn] = st.special;
-          }
-          st.pend_g[si] = g;
-          st.pend_d[si] = (uint32_t)d;
-          ++st.pend_n;
-          atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_deferred), 1ull);
-        }
-        block_sync();
-        mark(5);
-      }
-      return;
-    }
-    // ---------------- overflow path: too many distinct keys for the table.  Split the
-    // partition's key range into sub-ranges, each counted in its own table and ordered;
-    // the exclusive prefix is resolved first because the partial outputs are written
-    // before the total is known.  A sub-range narrower than the table holds fewer distinct
-    // keys than slots, so the splitting ends.
-    if (wid == 0) {
-      const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status, s.spin_limit);
-      if (lane == 0) st.excl = ex;
-    }
-    if (t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_overflow), 1ull);
-    K mn = EMPTY, mx = 0;
-    uint32_t sp = 0;  // the all-ones key, if present, is the largest key of all
-    for (uint64_t jb = 0; jb < nch_eff; jb += kRunBatch) {
-      const uint32_t nrb = (uint32_t)umin64(kRunBatch, nch_eff - jb);
-      if (!one_batch) load_runs(tb, f, nch_eff, jb, nc);
-      for (uint32_t r = wid; r < nrb; r += kCountThreads / 32) {
-        for (uint32_t i = lane; i < run_len[r]; i += 32) {
-          K key;
-          load_key_cg(src, (uint64_t)run_st[r] + i, key);
-          if (key != EMPTY) {
-            mn = key < mn ? key : mn;
-            mx = key > mx ? key : mx;
-          } else {
-            ++sp;
-          }
-        }
-      }
-      block_sync();
-    }
-    {
-      K a, cc;
-      block_range<K>(mn, mx, red_lo, red_hi, a, cc);
-      if (t == 0) {
-        st.stk_n = 0;
-        if (a <= cc) {
-          stk_lo[0] = a;
-          stk_hi[0] = cc;
-          st.stk_n = 1;
-        }
-      }
-    }
-    block_sync();
-    const int bTf = s.bT_max;
-    tb_.keys = reinterpret_cast<K*>(sm);
-    tb_.counts = reinterpret_cast<uint32_t*>(tb_.keys + cap_slots);
-    uint64_t written = 0;
-    while (st.stk_n > 0) {
-      const K lo = stk_lo[st.stk_n - 1], hi = stk_hi[st.stk_n - 1];
-      block_sync();
-      if (t == 0) {
-        --st.stk_n;
-        st.ovf = 0;
-        st.special = 0;
-        st.nnew = 0;
-      }
-      table_clear<KW>(tb_, cap_slots);
-      block_sync();
-      uint32_t claimed = 0;
-      for (uint64_t jb = 0; jb < nch_eff; jb += kRunBatch) {
-        const uint32_t nrb = (uint32_t)umin64(kRunBatch, nch_eff - jb);
-        if (!one_batch) load_runs(tb, f, nch_eff, jb, nc);
-        claimed += count_runs(tb_, src, nrb, true, lo, hi, bTf, false, check);
-        block_sync();
-      }
-      add_claimed(claimed);
-      block_sync();
-      const uint32_t dn2 = st.nnew;
-      const K width = hi - lo;
-      if (st.ovf || dn2 > dcap) {
-        if (t == 0) {
-          if (width == 0 || st.stk_n + 2 > 160) {
-            atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
-          } else {
-            const K mid = lo + (width >> 1);
-            stk_lo[st.stk_n] = mid + 1;
-            stk_hi[st.stk_n] = hi;
-            stk_lo[st.stk_n + 1] = lo;
-            stk_hi[st.stk_n + 1] = mid;
-            st.stk_n += 2;
-          }
-        }
-        block_sync();
-        continue;
-      }
-      const uint64_t base = st.excl + written;
-      {
-        uint32_t rank2[kRankRegs];
-        if (wid > 0) {
-          if (t == 32) {
-            range_s[0] = lo;
-            range_s[1] = hi;
-          }
-          K lo2;
-          int sh2;
-          uint32_t NB2;
-          bucket_slots<KW>(tb_, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &st.big_n, lo2, sh2, NB2,
-                           &b.meta->status);
-          rank_slots<KW>(tb_, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, st.big_n, rank2, nullptr);
-        }
-        block_sync();
-        if (wid > 0) emit_slots<KW>(tb_, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
-      }
-      written += dn2;
-      block_sync();
-    }
-    if (one_batch) discard_runs(src, nr);
-#pragma unroll
-    for (int dd = 16; dd > 0; dd >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, dd);
-    if (lane == 0) wtmp[wid] = sp;
-    block_sync();
-    if (t == 0) {
-      uint64_t tot = 0;
-      for (int w = 0; w < kCountThreads / 32; ++w) tot += wtmp[w];
-      if (tot) {
-        if (tot > 0xffffffffull) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
-        if (st.excl + written < s.cap) {
-          store_key(b.out_keys, st.excl + written, EMPTY);
-          b.out_counts[st.excl + written] = (uint32_t)tot;
-        } else {
-          atomicOr(&b.meta->status, ST_INTERNAL);
-        }
-        ++written;
-      }
-      if (!(s.withhold && g == 0)) st_status(&b.look[g], kLookIncl | (st.excl + written));
-      b.fhist[g] = (uint32_t)written;
-      prefetch();
-    }
-    block_sync();
-    mark(6);
-  }
-};
-
-template <int KW, bool MERGE>
-__device__ __forceinline__ void phase2_body(const Shape& s, const Buffers& b, uint32_t bid) {
+template <int KW, bool MERGE = false>
+__device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
-  __shared__ P2State st;
+  const uint32_t cap_slots = 1u << s.bT_max;
+  const uint32_t dcap = (3u * cap_slots) >> 2;  // most distinct keys a table is ordered with
+  uint32_t* hist = reinterpret_cast<uint32_t*>(sm + (size_t)cap_slots * (KW * 8 + 4));
+  uint16_t* idx = reinterpret_cast<uint16_t*>(hist + padded_len(hist_max(KW)));  // [dcap]
+  __shared__ uint64_t excl_s, next_s[3];  // next ticket, its input range
+  __shared__ volatile uint32_t ordered_s;  // the workers have ranked the current table
+  __shared__ uint32_t next_u[2];          // its range-map interval: [next_u[0], next_u[1] - 1]
+  __shared__ uint32_t ovf_s, special_s, nnew_s;
   __shared__ uint32_t wtmp[32];
   __shared__ K red_lo[32], red_hi[32];
   __shared__ K stk_lo[160], stk_hi[160];
   __shared__ K range_s[2];
-  __shared__ uint32_t big_s[kBigMax];
-  const int P1 = 1 << s.b1;
-  uint32_t* persist = reinterpret_cast<uint32_t*>(sm + phase2_area(KW, s.bT_max));
-  Phase2<KW, MERGE> p{s, b, sm, st, wtmp};
-  p.tstart_s = persist;
-  p.tsplit_s = persist + max_coarse(KW) + kStageLag + 1;
-  p.run_st = persist + 2 * (max_coarse(KW) + kStageLag) + 1;
-  p.run_len = p.run_st + kRunBatch;
-  p.run_pre = p.run_len + kRunBatch;
-  p.red_lo = red_lo;
-  p.red_hi = red_hi;
-  p.range_s = range_s;
-  p.stk_lo = stk_lo;
-  p.stk_hi = stk_hi;
-  p.big_s = big_s;
-  p.slots = b.stage + (size_t)bid * s.n_slots * s.stage_bytes;
-  p.P1 = P1;
-  p.cap_slots = 1u << s.bT_max;
-  p.dcap = (3u * p.cap_slots) >> 2;
-  const uint32_t t = threadIdx.x;
-  if (bid >= s.n_stage || s.b1 > max_coarse_log2(KW) || s.n_slots < 1 || s.n_slots > (uint32_t)kMaxSlots) {
-    if (t == 0) atomicOr(&b.meta->status, ST_INTERNAL);
-    return;
+  __shared__ uint32_t big_s[kBigMax], big_n;
+  __shared__ int stk_n;
+  const K EMPTY = all_ones<K>();
+  const uint64_t NF = min(b.meta->n_fine, s.nf_max);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long* prof = s.profile ? reinterpret_cast<unsigned long long*>(b.meta->sub_cycles) : nullptr;
+  unsigned long long* ticket = reinterpret_cast<unsigned long long*>(&b.meta->ticket);
+  // profiled plans: thread 0 adds the cycles spent in each phase (0 clear, 1 count, 2 -,
+  // 3 order, 4 look-back (warp 0, overlapped), 5 emit, 6 overflow path, 7 ticket + setup)
+  long long t_mark = clock64();
+  auto phase = [&](int i) {
+    if (s.profile && threadIdx.x == 0) {
+      const long long now = clock64();
+      atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[i]), (unsigned long long)(now - t_mark));
+      t_mark = now;
+    }
+  };
+  // The next partition's ticket, input range and range-map interval (next_s, next_u) are
+  // fetched by thread 0 while the workers write the current partition out: the ticket is
+  // taken as late as that, so that partitions start in ticket order and a look-back seldom
+  // waits on a predecessor that started late; the rest arrives by asynchronous copies to
+  // shared memory.  Tickets stay in increasing order within a block, so the block holding
+  // the smallest unfinished ticket is always working on it and every look-back ends.
+  auto fetch_next = [&](uint64_t nx) {  // one thread; completes at cp.async.wait_all
+    next_s[0] = nx;
+    if (nx < NF) {
+      cp_async8(&next_s[1], &b.foff[nx]);
+      cp_async8(&next_s[2], &b.foff[nx + 1]);
+      cp_async4(&next_u[0], &b.flo[nx]);
+      cp_async4(&next_u[1], &b.flo[nx + 1]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    ordered_s = 0;
+    fetch_next(atomicAdd(ticket, 1ull));
+    cp_async_wait_all();
   }
-  for (int i = t; i <= P1 + kStageLag; i += kCountThreads) p.tstart_s[i] = b.tstart[i];
-  for (int i = t; i < P1 + kStageLag; i += kCountThreads) p.tsplit_s[i] = b.tsplit[i];
-  if (t == 0) {
-    st.pend_head = 0;
-    st.pend_n = 0;
-    st.one = 1;
-    for (int i = 0; i < 8; ++i) st.acc[i] = st.tally[i] = 0;
-    st.tmark = clock64();
-  }
-  block_sync();
-  if (t == 0) p.prefetch();
   while (true) {
     block_sync();
-    const uint32_t kind = st.nx_kind;
-    if (kind == TASK_DONE) break;
-    const uint32_t c = st.nx_c, i = st.nx_i, m = st.nx_m, ulo = st.nx_ulo, uhi = st.nx_uhi;
-    const uint64_t cs = st.nx_cs, ce = st.nx_ce, tb = st.nx_tb, g = st.nx_g;
-    block_sync();  // the task is read: thread 0 may prepare the next one
-    p.mark(7);
-    if (kind == TASK_SPLIT) p.split(c, i, cs, ce, m, tb);
-    else p.count(c, i, g, cs, ce, tb, ulo, uhi);
-    while (p.finalize(false)) {  // the waiting runs whose prefix is known by now
+    const uint64_t g = next_s[0];
+    if (g >= NF) break;
+    const uint64_t f0 = next_s[1];
+    uint64_t n = next_s[2] - f0;
+    if (threadIdx.x == 0) {
+      ovf_s = 0;
+      special_s = 0;
+      nnew_s = 0;
     }
-  }
-  while (st.pend_n) p.finalize(true);
-  p.mark(7);
-  if (s.profile && t == 0) {
-    for (int i = 0; i < 8; ++i) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[i]), st.acc[i]);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->sub_cycles[i]), st.tally[i]);
+    if (f0 > s.cap || n > s.cap - f0) {  // inconsistent scan: record it, count nothing
+      if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+      n = 0;
+    }
+    const uint64_t* in = b.sbuf + f0 * KW;
+    // table: at least twice the keys (at most that many distinct), within the cap
+    int bT = 6;
+    while (bT < s.bT_max && ((uint64_t)1 << bT) < 2 * n) ++bT;
+    Table<KW> tb;
+    tb.keys = reinterpret_cast<K*>(sm);
+    tb.counts = reinterpret_cast<uint32_t*>(tb.keys + (1u << bT));
+    phase(7);
+    table_clear<KW>(tb, 1u << bT);
+    block_sync();
+    phase(0);
+    count_all<KW, MERGE>(tb, in, n, false, K(0), K(0), bT, s.k == 32 * KW, s.count_limit, &nnew_s, &ovf_s,
+                         &special_s, &b.meta->status);
+    block_sync();
+    phase(1);
+    const uint32_t dn = nnew_s;
+    if (!ovf_s && dn <= dcap) {
+      const uint64_t d = (uint64_t)dn + (special_s ? 1 : 0);
+      if (threadIdx.x == 0 && !(s.withhold && g == 0))
+        st_status(&b.look[g], (g == 0 && !s.defer_all ? kLookIncl : kLookAgg) | d);
+      // Warp 0 resolves the exclusive prefix (look-back) while the workers order the table,
+      // waiting on unpublished predecessors only as long as the workers are busy.  Without a
+      // prefix by then, the partition's run is written to its own input region instead
+      // (deferred) and k_compact moves it once all counts are known.
+      uint32_t rank[kRankRegs];
+      if (wid == 0) {
+        const long long lb0 = clock64();
+        // (with a withheld prefix, a test that needs the wait to run out, it does not give up
+        // when the ordering is done)
+        const uint64_t ex = s.defer_all ? kNoPrefix
+                            : g == 0    ? 0
+                                        : lookback(b.look, g, &b.meta->status, s.spin_limit,
+                                                   s.withhold ? nullptr : &ordered_s);
+        if (lane == 0) {
+          const bool direct = ex != kNoPrefix;
+          if (direct && g > 0) st_status(&b.look[g], kLookIncl | (ex + d));
+          b.fhist[g] = (uint32_t)d | (direct ? 0u : 0x80000000u);
+          if (!direct) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_deferred), 1ull);
+          excl_s = ex;
+          if (s.profile)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->phase_cycles[4]), (unsigned long long)(clock64() - lb0));
+        }
+      } else {
+        const long long tm = clock64();
+        if (threadIdx.x == 32) {
+          // every key of the partition lies in the key range of its range-map interval.
+          // next_u still holds this partition's interval (the next one is fetched during
+          // the write-out); flo[NF] = 0, so the last interval ends at 2^32 - 1
+          const uint32_t ulo = next_u[0], uhi = next_u[1] - 1u;
+          uint32_t xlo, xhi;
+          x_range(ulo, uhi, s.canonical, xlo, xhi);
+          key_range(xlo, xhi, s.k, range_s[0], range_s[1]);
+        }
+        K lo;
+        int sh;
+        uint32_t NB;
+        bucket_slots<KW>(tb, 1u << bT, dn, range_s, hist, idx, wtmp, big_s, &big_n, lo, sh, NB, &b.meta->status,
+                         prof);
+        if (prof && threadIdx.x == 32) atomicAdd(&prof[1], (unsigned long long)(clock64() - tm));
+        rank_slots<KW>(tb, idx, idx, dn, hist, NB, lo, sh, big_s, big_n, rank, prof);
+        bar_workers();
+        if (threadIdx.x == 32) ordered_s = 1;
+      }
+      block_sync();
+      phase(3);
+      const uint64_t ex = excl_s;
+      if (threadIdx.x == 0) {
+        ordered_s = 0;
+        fetch_next(atomicAdd(ticket, 1ull));
+      }
+      // direct: final positions; deferred: the partition's own input region
+      const bool direct = ex != kNoPrefix;
+      uint64_t* okeys = direct ? b.out_keys : b.sbuf;
+      uint32_t* ocnts = direct ? b.out_counts : reinterpret_cast<uint32_t*>(b.kbuf);
+      const uint64_t obase = direct ? ex : f0, olim = direct ? s.cap : f0 + n;
+      if (wid > 0) emit_slots<KW>(tb, idx, dn, rank, obase, okeys, ocnts, olim, &b.meta->status);
+      if (threadIdx.x == 0) {
+        if (special_s) {
+          if (obase + dn < olim) {
+            store_key(okeys, obase + dn, EMPTY);
+            ocnts[obase + dn] = special_s;
+          } else {
+            atomicOr(&b.meta->status, ST_INTERNAL);
+          }
+        }
+        cp_async_wait_all();
+      }
+      phase(5);
+    } else {
+      // ---------------- overflow path: too many distinct keys for the table.  Split the
+      // partition's key range into sub-ranges, each counted in its own table and ordered;
+      // the exclusive prefix is resolved first because the partial outputs are written
+      // before the total is known.  A sub-range narrower than the table holds fewer
+      // distinct keys than slots, so the splitting ends.
+      if (wid == 0) {
+        const uint64_t ex = g == 0 ? 0 : lookback(b.look, g, &b.meta->status, s.spin_limit);
+        if (lane == 0) excl_s = ex;
+      }
+      if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.meta->n_overflow), 1ull);
+      K mn = EMPTY, mx = 0;
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        K key;
+        load_key(in, i, key);
+        if (key != EMPTY) {
+          mn = key < mn ? key : mn;
+          mx = key > mx ? key : mx;
+        }
+      }
+      {
+        K a, c;
+        block_range<K>(mn, mx, red_lo, red_hi, a, c);
+        if (threadIdx.x == 0) {
+          stk_n = 0;
+          if (a <= c) {
+            stk_lo[0] = a;
+            stk_hi[0] = c;
+            stk_n = 1;
+          }
+        }
+      }
+      block_sync();
+      const int bTf = s.bT_max;
+      tb.keys = reinterpret_cast<K*>(sm);
+      tb.counts = reinterpret_cast<uint32_t*>(tb.keys + cap_slots);
+      uint64_t written = 0;
+      while (stk_n > 0) {
+        const K lo = stk_lo[stk_n - 1], hi = stk_hi[stk_n - 1];
+        block_sync();
+        if (threadIdx.x == 0) {
+          --stk_n;
+          ovf_s = 0;
+          special_s = 0;
+          nnew_s = 0;
+        }
+        table_clear<KW>(tb, cap_slots);
+        block_sync();
+        count_all<KW, MERGE>(tb, in, n, true, lo, hi, bTf, s.k == 32 * KW, s.count_limit, &nnew_s, &ovf_s,
+                             &special_s, &b.meta->status);
+        block_sync();
+        const uint32_t dn2 = nnew_s;
+        const K width = hi - lo;
+        if (ovf_s || dn2 > dcap) {
+          if (threadIdx.x == 0) {
+            if (width == 0 || stk_n + 2 > 160) {
+              atomicOr(&b.meta->status, ST_INTERNAL);  // a single key cannot overflow
+            } else {
+              const K mid = lo + (width >> 1);
+              stk_lo[stk_n] = mid + 1;
+              stk_hi[stk_n] = hi;
+              stk_lo[stk_n + 1] = lo;
+              stk_hi[stk_n + 1] = mid;
+              stk_n += 2;
+            }
+          }
+          block_sync();
+          continue;
+        }
+        const uint64_t base = excl_s + written;
+        {
+          uint32_t rank2[kRankRegs];
+          if (wid > 0) {
+            if (threadIdx.x == 32) {
+              range_s[0] = lo;
+              range_s[1] = hi;
+            }
+            K lo2;
+            int sh2;
+            uint32_t NB2;
+            bucket_slots<KW>(tb, cap_slots, dn2, range_s, hist, idx, wtmp, big_s, &big_n, lo2, sh2, NB2,
+                             &b.meta->status);
+            rank_slots<KW>(tb, idx, idx, dn2, hist, NB2, lo2, sh2, big_s, big_n, rank2, nullptr);
+          }
+          block_sync();
+          if (wid > 0) emit_slots<KW>(tb, idx, dn2, rank2, base, b.out_keys, b.out_counts, s.cap, &b.meta->status);
+        }
+        written += dn2;
+        block_sync();
+      }
+      // the all-ones key, if present, is the largest key of all
+      uint32_t sp = 0;
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        K key;
+        load_key(in, i, key);
+        sp += key == EMPTY;
+      }
+  #pragma unroll
+      for (int dd = 16; dd > 0; dd >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, dd);
+      if (lane == 0) wtmp[wid] = sp;
+      block_sync();
+      if (threadIdx.x == 0) {
+        uint64_t tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wtmp[w];
+        if (tot) {
+          if (tot > s.count_limit) atomicOr(&b.meta->status, ST_COUNT_OVERFLOW);
+          if (excl_s + written < s.cap) {
+            store_key(b.out_keys, excl_s + written, EMPTY);
+            b.out_counts[excl_s + written] = (uint32_t)tot;
+          } else {
+            atomicOr(&b.meta->status, ST_INTERNAL);
+          }
+          ++written;
+        }
+        if (!(s.withhold && g == 0)) st_status(&b.look[g], kLookIncl | (excl_s + written));
+        b.fhist[g] = (uint32_t)written;
+        fetch_next(atomicAdd(ticket, 1ull));
+        cp_async_wait_all();
+      }
+      phase(6);
     }
   }
 }
-
 template <int KW, bool MERGE = false>
-__global__ void __launch_bounds__(kCountThreads, 1) k_phase2(Shape s, Buffers b) {
-  phase2_body<KW, MERGE>(s, b, blockIdx.x);
+__global__ void __launch_bounds__(kCountThreads, kCountBlocksPerSM) k_count_emit(Shape s, Buffers b) {
+  count_emit_body<KW, MERGE>(s, b);
 }
 template <int KW>
-__global__ void __launch_bounds__(kCountThreads, 1) k_phase2_batch(BatchTab t) {
+__global__ void __launch_bounds__(kCountThreads, kCountBlocksPerSM) k_count_emit_batch(BatchTab t) {
   KC_BATCH_PROLOGUE(t);
-  phase2_body<KW, false>(d.s, d.b, bid);
+  count_emit_body<KW>(d.s, d.b);
 }
 
-// ------------------------------------------------------------------ final: the output size
+// ------------------------------------------------------------------ final: offsets of the runs
 // Exclusive scan of the distinct counts of the fine partitions (one block of 1024
-// threads): every look-back word must hold its partition's inclusive prefix, and the total
-// is the number of distinct keys.
+// threads): fcur[g] = first output position of partition g, n_distinct = the total.  The
+// look-back words are checked against it, and the deferred partitions are listed (in
+// increasing order) at the front of the spent look-back array for k_compact.
 __device__ __forceinline__ void scan_distinct_body(const Shape& sh, const Buffers& b) {
   __shared__ uint64_t wt[32];
+  __shared__ uint32_t wd[32];
   __shared__ uint64_t carry_s;
+  __shared__ uint32_t dcarry_s;
   const uint64_t NF = min(b.meta->n_fine, sh.nf_max);
   const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
-  if (t == 0) carry_s = 0;
+  if (t == 0) {
+    carry_s = 0;
+    dcarry_s = 0;
+  }
   __syncthreads();
   bool bad = false;
   for (uint64_t base = 0; base < NF; base += (uint64_t)nt * 8) {
     uint32_t v[8];
     unsigned long long lk[8];
     uint64_t s = 0;
+    uint32_t nd = 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const uint64_t i = base + (uint64_t)t * 8 + m;
       v[m] = i < NF ? b.fhist[i] : 0;
       lk[m] = i < NF ? ld_status(&b.look[i]) : 0;
-      s += v[m];
+      s += v[m] & 0x7fffffffu;
+      nd += v[m] >> 31;
     }
     uint64_t x = s;
+    uint32_t y = nd;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint64_t xs = __shfl_up_sync(0xffffffffu, x, d);
-      if (lane >= d) x += xs;
+      const uint32_t ys = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) {
+        x += xs;
+        y += ys;
+      }
     }
-    if (lane == 31) wt[wid] = x;
-    __syncthreads();
+    if (lane == 31) {
+      wt[wid] = x;
+      wd[wid] = y;
+    }
+    __syncthreads();  // also: every look-back word of this chunk has been read
     if (wid == 0) {
       uint64_t w = wt[lane];
+      uint32_t z = wd[lane];
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const uint64_t ws = __shfl_up_sync(0xffffffffu, w, d);
-        if (lane >= d) w += ws;
+        const uint32_t zs = __shfl_up_sync(0xffffffffu, z, d);
+        if (lane >= d) {
+          w += ws;
+          z += zs;
+        }
       }
       wt[lane] = w;
+      wd[lane] = z;
     }
     __syncthreads();
     uint64_t run = carry_s + x - s + (wid ? wt[wid - 1] : 0);
+    uint32_t drun = dcarry_s + y - nd + (wid ? wd[wid - 1] : 0);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const uint64_t i = base + (uint64_t)t * 8 + m;
       if (i < NF) {
-        run += v[m];
-        bad |= lk[m] != (kLookIncl | run);
+        const uint64_t d = v[m] & 0x7fffffffu;
+        const bool deferred = v[m] >> 31;
+        // a direct partition published its inclusive prefix, a deferred one its count
+        const uint64_t want = deferred ? (kLookAgg | d) : (kLookIncl | (run + d));
+        bad |= lk[m] != want;
+        b.fcur[i] = run;
+        if (deferred) b.look[drun++] = i;
+        run += d;
       }
     }
     __syncthreads();
-    if (t == 0) carry_s += wt[31];
+    if (t == 0) {
+      carry_s += wt[31];
+      dcarry_s += wd[31];
+    }
     __syncthreads();
   }
   if (bad) atomicOr(&b.meta->status, ST_INTERNAL);
-  if (t == 0) b.meta->n_distinct = carry_s;
+  if (t == 0) {
+    b.meta->n_distinct = carry_s;
+    if (dcarry_s != b.meta->n_deferred) atomicOr(&b.meta->status, ST_INTERNAL);
+  }
 }
 __global__ void __launch_bounds__(1024) k_scan_distinct(Shape sh, Buffers b) { scan_distinct_body(sh, b); }
 __global__ void __launch_bounds__(1024) k_scan_distinct_batch(BatchTab t) {
@@ -2352,11 +2198,52 @@ __global__ void __launch_bounds__(1024) k_scan_distinct_batch(BatchTab t) {
   scan_distinct_body(d.s, d.b);
 }
 
+// Move the runs of the deferred fine partitions from their input regions (keys in sbuf,
+// counts in kbuf as 32-bit words) to their output positions: one block per partition.
+template <int KW>
+__device__ __forceinline__ void compact_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
+  typedef typename KeyT<KW>::T K;
+  const uint64_t n_def = min(b.meta->n_deferred, s.nf_max);
+  const uint32_t* cnt_src = reinterpret_cast<const uint32_t*>(b.kbuf);
+  for (uint64_t q = bid; q < n_def; q += nblk) {
+    const uint64_t g = b.look[q];
+    if (g >= min(b.meta->n_fine, s.nf_max)) {
+      if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+      continue;
+    }
+    const uint32_t d = b.fhist[g] & 0x7fffffffu;
+    const uint64_t src = b.foff[g], dst = b.fcur[g];
+    if (src + d > s.cap || dst + d > s.cap) {
+      if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
+      continue;
+    }
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+      K key;
+      load_key(b.sbuf, src + i, key);
+      store_key(b.out_keys, dst + i, key);
+      b.out_counts[dst + i] = cnt_src[src + i];
+    }
+  }
+}
+template <int KW>
+__global__ void __launch_bounds__(256) k_compact(Shape s, Buffers b) {
+  compact_body<KW>(s, b, blockIdx.x, gridDim.x);
+}
+template <int KW>
+__global__ void __launch_bounds__(256) k_compact_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  compact_body<KW>(d.s, d.b, bid, nblk);
+}
+
 // ------------------------------------------------------------------ launches
 constexpr size_t kScatterStaticSmem = 9216;  // pass B's static shared memory (batched form included), rounded up
 static size_t scatter_smem(int kw, int nt, int P1, bool keep_c) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
   return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4 + (keep_c ? sub * 4 : 0);
+}
+static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 8 + kFineLocalCap * 4 + 16; }
+static size_t fine_scatter_smem(int kw, int P1) {
+  return (size_t)kFineChunk * (kw * 8 + 2) + kFineLocalCap * (8 + 4 + 4) + (size_t)(P1 + 1) * 8 + 16;
 }
 
 int configure_kernels(int device) {
@@ -2381,10 +2268,14 @@ int configure_kernels(int device) {
   KC_SET(k_scatter_direct<1>);
   KC_SET(k_scatter_direct<2>);
   KC_SET(k_fine_plan);
-  KC_SET(k_phase2<1>);
-  KC_SET(k_phase2<2>);
-  KC_SET((k_phase2<1, true>));
-  KC_SET((k_phase2<2, true>));
+  KC_SET(k_fine_hist<1>);
+  KC_SET(k_fine_hist<2>);
+  KC_SET(k_fine_scatter<1>);
+  KC_SET(k_fine_scatter<2>);
+  KC_SET(k_count_emit<1>);
+  KC_SET(k_count_emit<2>);
+  KC_SET((k_count_emit<1, true>));
+  KC_SET((k_count_emit<2, true>));
   KC_SET(k_bucket_scan);
   KC_SET(k_pack_count_batch<1>);
   KC_SET(k_pack_count_batch<2>);
@@ -2393,8 +2284,12 @@ int configure_kernels(int device) {
   KC_SET((k_scatter_batch<1, 256, true>));
   KC_SET((k_scatter_batch<2, 256, true>));
   KC_SET(k_fine_plan_batch);
-  KC_SET(k_phase2_batch<1>);
-  KC_SET(k_phase2_batch<2>);
+  KC_SET(k_fine_hist_batch<1>);
+  KC_SET(k_fine_hist_batch<2>);
+  KC_SET(k_fine_scatter_batch<1>);
+  KC_SET(k_fine_scatter_batch<2>);
+  KC_SET(k_count_emit_batch<1>);
+  KC_SET(k_count_emit_batch<2>);
   KC_SET(k_bucket_scan_batch);
 #undef KC_SET
   return 0;
@@ -2435,7 +2330,7 @@ int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, con
   return launches;
 }
 
-int launch_phase2(const Shape& s, const Buffers& b, int n_sms, void* stream, const Marker& mark) {
+int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, void* stream, const Marker& mark) {
   cudaStream_t st = (cudaStream_t)stream;
   const int P1 = 1 << s.b1;
   int launches = 0;
@@ -2454,7 +2349,7 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, void* stream, con
     const bool keep_c = per_sm >= 2;
     const unsigned gt = (unsigned)s.n_tiles;
     if (s.aggr & kAggrNoSmemBuckets) {
-      k_direct_cursors<<<(P1 + 255) / 256, 256, 0, st>>>(b.cstart, reinterpret_cast<unsigned long long*>(b.toff), P1);
+      k_direct_cursors<<<(P1 + 255) / 256, 256, 0, st>>>(b.cstart, b.fcur, P1);
       ++launches;
       KC_STEP("k_direct_cursors");
       if (s.kw == 1) k_scatter_direct<1><<<gt, 256, smB, st>>>(s, b);
@@ -2469,25 +2364,40 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, void* stream, con
     ++launches;
     KC_STEP("k_scatter");
   }
-  k_fine_plan<<<1, 1024, (size_t)(P1 + kStageLag + 1) * 8, st>>>(s, b);
+  k_fine_plan<<<1, 1024, (size_t)P1 * 8, st>>>(b.cstart, b.hll, b.fine_base, b.fine_m, b.flo, P1, s.b1, s.fine_target, nf_max,
+                                               b.meta);
   ++launches;
   KC_STEP("k_fine_plan");
-  // the persistent split + count kernel: one block per SM (at most one per stage slot)
-  const unsigned gp = (unsigned)(s.n_stage < (uint32_t)n_sms ? s.n_stage : (uint32_t)n_sms);
-  const size_t smC = phase2_smem(s.kw, s.bT_max);
+  const unsigned gf = (unsigned)(n_sms * 2);
+  if (s.kw == 1) k_fine_hist<1><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);
+  else k_fine_hist<2><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);
+  ++launches;
+  KC_STEP("k_fine_hist");
+  k_fine_scan<<<1, 1024, 0, st>>>(s, b);
+  ++launches;
+  KC_STEP("k_fine_scan");
+  if (s.kw == 1) k_fine_scatter<1><<<gf, kFineThreads, fine_scatter_smem(1, P1), st>>>(s, b);
+  else k_fine_scatter<2><<<gf, kFineThreads, fine_scatter_smem(2, P1), st>>>(s, b);
+  ++launches;
+  KC_STEP("k_fine_scatter");
+  const size_t smC = count_kernel_smem(s.kw, s.bT_max, s.tail);
   if (s.aggr & kAggrWarpMerge) {
-    if (s.kw == 1) k_phase2<1, true><<<gp, kCountThreads, smC, st>>>(s, b);
-    else k_phase2<2, true><<<gp, kCountThreads, smC, st>>>(s, b);
+    if (s.kw == 1) k_count_emit<1, true><<<(unsigned)(n_sms * kCountBlocksPerSM), kCountThreads, smC, st>>>(s, b);
+    else k_count_emit<2, true><<<(unsigned)(n_sms * kCountBlocksPerSM), kCountThreads, smC, st>>>(s, b);
   } else if (s.kw == 1) {
-    k_phase2<1><<<gp, kCountThreads, smC, st>>>(s, b);
+    k_count_emit<1><<<(unsigned)(n_sms * kCountBlocksPerSM), kCountThreads, smC, st>>>(s, b);
   } else {
-    k_phase2<2><<<gp, kCountThreads, smC, st>>>(s, b);
+    k_count_emit<2><<<(unsigned)(n_sms * kCountBlocksPerSM), kCountThreads, smC, st>>>(s, b);
   }
   ++launches;
-  KC_STEP("k_phase2");
+  KC_STEP("k_count_emit");
   k_scan_distinct<<<1, 1024, 0, st>>>(s, b);
   ++launches;
   KC_STEP("k_scan_distinct");
+  if (s.kw == 1) k_compact<1><<<(unsigned)(n_sms * 8), 256, 0, st>>>(s, b);
+  else k_compact<2><<<(unsigned)(n_sms * 8), 256, 0, st>>>(s, b);
+  ++launches;
+  KC_STEP("k_compact");
   return launches;
 }
 
@@ -2501,12 +2411,14 @@ uint32_t batch_blocks(BatchKernel k, const Shape& s, int n_sms, uint64_t bases_t
     case BK_PACK: return (uint32_t)s.n_tiles;
     case BK_COL_SCAN: return s.n_tiles ? (uint32_t)((P1 + 31) / 32) : 0u;
     case BK_SCATTER: return (uint32_t)s.n_tiles;
-    case BK_PHASE2: {
+    case BK_FINE_HIST:
+    case BK_FINE_SCATTER: return clampu((s.L + 4ull * kFineChunk - 1) / (4ull * kFineChunk), 1, 2 * nsm);
+    case BK_COUNT: {
       const double share = bases_total ? (double)s.L / (double)bases_total : 1.0;
-      const uint64_t cap = nsm < s.n_stage ? nsm : s.n_stage;
-      return clampu((uint64_t)(2.0 * (double)nsm * share + 0.999), 1, cap);
+      return clampu((uint64_t)(2.0 * (double)nsm * share + 0.999), 1, nsm * kCountBlocksPerSM);
     }
-    default: return 1u;  // one block per count: bucket scan, fine plan, scan of distinct counts
+    case BK_COMPACT: return clampu(s.nf_max / 8, 1, 8 * nsm);
+    default: return 1u;  // one block per count: bucket scan, fine plan, fine scan, scan of distinct counts
   }
 }
 
@@ -2557,21 +2469,45 @@ int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mar
     ++launches;
     KC_STEP("k_scatter");
   }
-  KC_BLAUNCH(BK_FINE_PLAN,
-             (k_fine_plan_batch<<<bp.grid[BK_FINE_PLAN], 1024, (size_t)(P1 + kStageLag + 1) * 8, st>>>(
-                 tab(BK_FINE_PLAN))),
+  KC_BLAUNCH(BK_FINE_PLAN, (k_fine_plan_batch<<<bp.grid[BK_FINE_PLAN], 1024, (size_t)P1 * 8, st>>>(tab(BK_FINE_PLAN))),
              "k_fine_plan");
-  const size_t smC = phase2_smem(bp.kw, s0.bT_max);
   if (bp.kw == 1) {
-    KC_BLAUNCH(BK_PHASE2, (k_phase2_batch<1><<<bp.grid[BK_PHASE2], kCountThreads, smC, st>>>(tab(BK_PHASE2))),
-               "k_phase2");
+    KC_BLAUNCH(BK_FINE_HIST,
+               (k_fine_hist_batch<1><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
+               "k_fine_hist");
   } else {
-    KC_BLAUNCH(BK_PHASE2, (k_phase2_batch<2><<<bp.grid[BK_PHASE2], kCountThreads, smC, st>>>(tab(BK_PHASE2))),
-               "k_phase2");
+    KC_BLAUNCH(BK_FINE_HIST,
+               (k_fine_hist_batch<2><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
+               "k_fine_hist");
+  }
+  KC_BLAUNCH(BK_FINE_SCAN, (k_fine_scan_batch<<<bp.grid[BK_FINE_SCAN], 1024, 0, st>>>(tab(BK_FINE_SCAN))), "k_fine_scan");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_FINE_SCATTER,
+               (k_fine_scatter_batch<1><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(1, P1), st>>>(
+                   tab(BK_FINE_SCATTER))),
+               "k_fine_scatter");
+  } else {
+    KC_BLAUNCH(BK_FINE_SCATTER,
+               (k_fine_scatter_batch<2><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(2, P1), st>>>(
+                   tab(BK_FINE_SCATTER))),
+               "k_fine_scatter");
+  }
+  const size_t smC = count_kernel_smem(bp.kw, s0.bT_max, s0.tail);
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_COUNT, (k_count_emit_batch<1><<<bp.grid[BK_COUNT], kCountThreads, smC, st>>>(tab(BK_COUNT))),
+               "k_count_emit");
+  } else {
+    KC_BLAUNCH(BK_COUNT, (k_count_emit_batch<2><<<bp.grid[BK_COUNT], kCountThreads, smC, st>>>(tab(BK_COUNT))),
+               "k_count_emit");
   }
   KC_BLAUNCH(BK_SCAN_DISTINCT,
              (k_scan_distinct_batch<<<bp.grid[BK_SCAN_DISTINCT], 1024, 0, st>>>(tab(BK_SCAN_DISTINCT))),
              "k_scan_distinct");
+  if (bp.kw == 1) {
+    KC_BLAUNCH(BK_COMPACT, (k_compact_batch<1><<<bp.grid[BK_COMPACT], 256, 0, st>>>(tab(BK_COMPACT))), "k_compact");
+  } else {
+    KC_BLAUNCH(BK_COMPACT, (k_compact_batch<2><<<bp.grid[BK_COMPACT], 256, 0, st>>>(tab(BK_COMPACT))), "k_compact");
+  }
 #undef KC_BLAUNCH
   return launches;
 }

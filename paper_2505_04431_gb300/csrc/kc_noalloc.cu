@@ -34,6 +34,7 @@ struct DeviceSetup {
   void* scratch = nullptr;  // device address of kc_noalloc_scratch on this device
   int n_sms = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;
 };
 
 std::mutex g_setup_mu;
@@ -65,15 +66,17 @@ kc_status setup_device(int dev, DeviceSetup** out) {
     cudaError_t e = cudaGetSymbolAddress(&p, kc_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr)
       return nfail(KC_ECUDA, std::string("kc_count_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    int sms = 0, optin = 0;
+    int sms = 0, optin = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
       return nfail(KC_ECUDA, std::string("kc_count_noalloc: device attributes: ") + cudaGetErrorString(e));
     const int ce = kc::configure_kernels(dev);
     if (ce) return nfail(KC_ECUDA, std::string("kc_count_noalloc: kernel attributes: ") + cudaGetErrorString((cudaError_t)ce));
     d.scratch = p;
     d.n_sms = sms;
     d.smem_optin = (size_t)optin;
+    d.smem_per_sm = (size_t)per_sm;
     d.ready = true;
   }
   *out = &d;
@@ -122,7 +125,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   // shape and scratch layout: the same choices kc_count makes for this input size
   kc::ShapeOpts so;
   so.smem_optin = ds->smem_optin;
-  so.n_sms = ds->n_sms;
+  so.smem_per_sm = ds->smem_per_sm;
   kc::Shape s{};
   kc::Layout lay{};
   kc::make_shape(so, L, n_reads, k, canonical, false, false, s, lay);
@@ -140,7 +143,7 @@ extern "C" kc_status kc_count_noalloc(const uint8_t* reads, const uint64_t* offs
   kc::Marker none;
   int launches = kc::launch_phase1(s, b, ds->n_sms, (void*)strm, none);
   if (launches >= 0) {
-    const int l2 = kc::launch_phase2(s, b, ds->n_sms, (void*)strm, none);
+    const int l2 = kc::launch_phase2(s, b, ds->n_sms, (uint32_t)s.nf_max, (void*)strm, none);
     launches = l2 >= 0 ? launches + l2 : l2;
   }
   kc::Meta m{};

@@ -9,7 +9,7 @@ No part of the counting happens here: this module only times calls into the libr
 """
 from __future__ import annotations
 
-MAX_PARTITIONS = 2048
+MAX_PARTITIONS = 4096
 TABLE_LOADS = (0.45, 0.55)
 
 

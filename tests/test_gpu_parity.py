@@ -186,8 +186,8 @@ def test_overflow_path_forced(torch_cuda):
 
 
 def test_deferred_write_out_forced(torch_cuda):
-    # every fine partition leaves its run in its thread block's stage and writes it out once
-    # its offset is known (the path of a partition whose output offset was not yet known)
+    # every fine partition writes its run to its own input region and the compaction pass
+    # moves it to its place (the path of a partition whose output offset was not yet known)
     from paper_2505_04431_gb300 import KmerCounter
     c = KmerCounter(defer_all=True)
     try:
@@ -203,7 +203,7 @@ def test_deferred_write_out_forced(torch_cuda):
     finally:
         c.close()
     # with tiny tables too: overflowing partitions (which wait for their offset) among
-    # deferred ones (which publish their inclusive prefix only when they write out)
+    # deferred ones (which never publish an inclusive prefix)
     c = KmerCounter(defer_all=True, table_slots_max=64)
     try:
         reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.02)
@@ -214,7 +214,7 @@ def test_deferred_write_out_forced(torch_cuda):
         c.close()
 
 
-@pytest.mark.parametrize("hint", [1, 2048])
+@pytest.mark.parametrize("hint", [1, 4096])
 def test_partition_count_extremes(torch_cuda, hint):
     from paper_2505_04431_gb300 import KmerCounter
     c = KmerCounter(n_partitions_hint=hint)

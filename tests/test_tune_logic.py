@@ -37,9 +37,9 @@ def test_partition_candidates_stay_in_range():
     timer, seen = fake_timer({}, p1=1)
     tune.autotune(None, None, 31, timer=timer)
     assert {"n_partitions_hint": 0} not in seen and {"n_partitions_hint": 2} in seen
-    timer, seen = fake_timer({}, p1=2048)
+    timer, seen = fake_timer({}, p1=4096)
     tune.autotune(None, None, 31, timer=timer)
-    assert {"n_partitions_hint": 4096} not in seen and {"n_partitions_hint": 1024} in seen
+    assert {"n_partitions_hint": 8192} not in seen and {"n_partitions_hint": 2048} in seen
 
 
 def test_options_that_change_the_result_are_refused():

@@ -88,3 +88,27 @@ def test_noalloc_rejects_inputs_beyond_its_maximum(env):
                               ctypes.byref(nd), ctypes.byref(nv), torch.cuda.current_stream().cuda_stream)
     assert st == KC_EINVAL
     assert "maximum" in lib.kc_last_error().decode()
+
+
+def test_noalloc_refuses_misaligned_buffers_before_launching(env):
+    """A caller buffer at an odd offset (a slice of a larger tensor, say) is refused on the
+    host: the kernels write 16-byte keys for k > 32, 4-byte counts and read 8-byte offsets."""
+    torch, lib, _ = env
+    from paper_2505_04431_gb300 import KC_EINVAL
+    reads, offsets = synth.generate(synth.UNIFORM_SHORT, 1001, 0.01)[:2]
+    r = torch.from_numpy(reads).cuda()
+    o = torch.from_numpy(offsets.view(np.int64)).cuda()
+    cap = len(reads)
+    big_k = torch.zeros(cap * 2 + 4, dtype=torch.int64, device="cuda")
+    big_c = torch.zeros(cap + 4, dtype=torch.int32, device="cuda")
+    big_o = torch.zeros(len(offsets) * 8 + 8, dtype=torch.uint8, device="cuda")
+    nd, nv = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    cases = [(63, o.data_ptr(), big_k.data_ptr() + 8, big_c.data_ptr()),   # keys 8- but not 16-byte aligned
+             (31, o.data_ptr(), big_k.data_ptr() + 4, big_c.data_ptr()),   # keys not 8-byte aligned
+             (31, o.data_ptr(), big_k.data_ptr(), big_c.data_ptr() + 2),   # counts not 4-byte aligned
+             (31, big_o.data_ptr() + 4, big_k.data_ptr(), big_c.data_ptr())]  # offsets not 8-byte aligned
+    for k, op, kp, cp in cases:
+        st = lib.kc_count_noalloc(r.data_ptr(), op, len(offsets) - 1, k, 1, kp, cp, cap, ctypes.byref(nd),
+                                  ctypes.byref(nv), stream)
+        assert st == KC_EINVAL and "aligned" in lib.kc_last_error().decode()
