@@ -133,6 +133,17 @@ kc_status kc_free(kc_plan_t plan, kc_result *res);
  * counts_host n uint32.  Synchronous.  Errors: KC_EINVAL, KC_ECUDA. */
 kc_status kc_result_copy_to_host(kc_plan_t plan, const kc_result *res, uint64_t *keys_host, uint32_t *counts_host);
 
+/* Device memory a count of n_reads reads and n_bases bases with this k would take on this
+ * plan: *scratch_bytes for its working buffers (a plan keeps one scratch block, grown to the
+ * largest count it has run, and reuses it) and *result_bytes for the result buffers it
+ * allocates (held until kc_free).  reads_on_device / offsets_on_device: whether the inputs
+ * will be passed as device memory (16-byte aligned reads), so that no staging copy is
+ * counted.  Host arithmetic only (the rules kc_count sizes a count by); nothing is
+ * allocated.  Serves admission control: a server admits a request when free device memory
+ * covers it.  Errors: KC_EINVAL (NULL arguments, k outside 1..64). */
+kc_status kc_footprint(kc_plan_t plan, uint64_t n_reads, uint64_t n_bases, int k, int reads_on_device,
+                       int offsets_on_device, uint64_t *scratch_bytes, uint64_t *result_bytes);
+
 /* Destroy a plan and its scratch memory.  Results must be freed first. */
 kc_status kc_plan_destroy(kc_plan_t plan);
 

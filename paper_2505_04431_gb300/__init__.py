@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
             "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch",
-            "kc_submit", "kc_job_poll", "kc_job_wait", "kc_submit_batch"]
+            "kc_submit", "kc_job_poll", "kc_job_wait", "kc_submit_batch", "kc_footprint"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 KC_PLAN_DEFER_ALL = 2
@@ -111,6 +111,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.kc_job_wait.restype = i32
     lib.kc_submit_batch.argtypes = [vp, ctypes.c_uint32, P(vp), P(vp), P(u64), P(u64), i32, i32, P(u64)]
     lib.kc_submit_batch.restype = i32
+    lib.kc_footprint.argtypes = [vp, u64, u64, i32, i32, i32, P(u64), P(u64)]
+    lib.kc_footprint.restype = i32
     _lib = lib
     return lib
 
@@ -357,6 +359,16 @@ class KmerCounter:
         finally:
             self._inflight.pop(int(job), None)
         return CountResult(self, res)
+
+    def footprint(self, n_reads: int, n_bases: int, k: int, reads_on_device: bool = True,
+                  offsets_on_device: bool = True) -> tuple[int, int]:
+        """(scratch bytes, result bytes) a count of this size would take on this plan
+        (kc_footprint; host arithmetic, nothing allocated)."""
+        sb, rb = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib, self._lib.kc_footprint(self._plan, int(n_reads), int(n_bases), int(k),
+                                                 int(bool(reads_on_device)), int(bool(offsets_on_device)),
+                                                 ctypes.byref(sb), ctypes.byref(rb)))
+        return int(sb.value), int(rb.value)
 
     def stats(self) -> dict:
         st = Stats()

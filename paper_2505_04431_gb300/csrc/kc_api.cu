@@ -700,6 +700,19 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   return KC_OK;
 }
 
+kc_status kc_footprint(kc_plan_t p, uint64_t n_reads, uint64_t n_bases, int k, int reads_on_device,
+                       int offsets_on_device, uint64_t* scratch_bytes, uint64_t* result_bytes) {
+  g_err.clear();
+  if (!p || !scratch_bytes || !result_bytes) return fail(KC_EINVAL, "kc_footprint: NULL argument");
+  if (k < 1 || k > 64) return fail(KC_EINVAL, "kc_footprint: k must be in 1..64");
+  kc::Shape s{};
+  kc::Layout lay{};
+  kc::make_shape(shape_opts(p), n_bases, n_reads, k, 1, n_bases > 0 && !reads_on_device, !offsets_on_device, s, lay);
+  *scratch_bytes = lay.total;
+  *result_bytes = s.cap * s.kw * 8 + s.cap * 4;
+  return KC_OK;
+}
+
 kc_status kc_free(kc_plan_t p, kc_result* r) {
   g_err.clear();
   if (!p || !r) return fail(KC_EINVAL, "kc_free: NULL argument");

@@ -127,17 +127,6 @@ __device__ __forceinline__ unsigned long long ld_status(const unsigned long long
   return v;
 }
 
-// Two adjacent 64-bit words of shared memory in one 16-byte load, read fresh (volatile):
-// other threads of the block may be claiming them.
-__device__ __forceinline__ ulonglong2 ld_pair_shared(const uint64_t* p) {
-  ulonglong2 v;
-  asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];"
-               : "=l"(v.x), "=l"(v.y)
-               : "r"((uint32_t)__cvta_generic_to_shared(p))
-               : "memory");
-  return v;
-}
-
 __device__ __forceinline__ u128 cas128_shared(u128* p, u128 cmp, u128 val) {
   uint64_t clo = (uint64_t)cmp, chi = (uint64_t)(cmp >> 64), vlo = (uint64_t)val, vhi = (uint64_t)(val >> 64), olo, ohi;
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
@@ -1390,11 +1379,9 @@ constexpr int kProbeLimit = 128;
 constexpr int kWorkers = kCountThreads - 32;  // warps 1.. load and sort while warp 0 looks back
 constexpr int kSlotsPerWorker = ((1 << kTableLog2Cap) + kWorkers - 1) / kWorkers;
 
-// counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes).
-// 64-bit keys start their probe sequence at an even slot, so that its first two slots are
-// one aligned 16-byte pair that a single shared-memory load reads.
+// counting-table slot of a key: a multiplicative hash (spreads keys that share prefixes)
 __device__ __forceinline__ uint32_t hslot(uint64_t key, int bT) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bT)) & ~1u;
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bT));
 }
 __device__ __forceinline__ uint32_t hslot(u128 key, int bT) {
   const uint64_t h = ((uint64_t)key ^ ((uint64_t)(key >> 64) * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull;
@@ -1513,34 +1500,7 @@ __device__ void count_all(Table<KW> tb, const uint64_t* in, uint64_t n, bool ran
         if (full_width && key == EMPTY) {
           if (atomicAdd(special, 1u) >= limit) atomicOr(status, ST_COUNT_OVERFLOW);
         } else {
-          int r = 0;
-          if constexpr (KW == 1) {
-            // the key's home pair, read at once: most keys are there already or claim a free
-            // slot of it; the others go on along the probe sequence
-            const uint32_t h = hslot(key, bT);
-            uint64_t* pk = reinterpret_cast<uint64_t*>(tb.keys);
-            const ulonglong2 v = ld_pair_shared(pk + h);
-            uint32_t sl = h;
-            if (v.x == (uint64_t)key) {
-              r = 1;
-            } else if (v.y == (uint64_t)key) {
-              r = 1;
-              sl = h + 1;
-            } else if (v.x == ~0ull || v.y == ~0ull) {
-              sl = v.x == ~0ull ? h : h + 1;
-              const unsigned long long old =
-                  atomicCAS(reinterpret_cast<unsigned long long*>(pk + sl), ~0ull, (unsigned long long)key);
-              r = old == ~0ull ? 2 : (old == (unsigned long long)key ? 1 : 0);
-            }
-            if (r) {
-              if (check) {
-                if (atomicAdd(&tb.counts[sl], 1u) >= limit) atomicOr(status, ST_COUNT_OVERFLOW);
-              } else {
-                atomicAdd(&tb.counts[sl], 1u);  // result unused: a reduction
-              }
-            }
-          }
-          if (!r) r = count_insert<KW>(tb, key, 1u, bT, check, limit, status);
+          const int r = count_insert<KW>(tb, key, 1u, bT, check, limit, status);
           if (!r) atomicOr(ovf, 1u);
           claimed += r == 2;
         }

@@ -283,3 +283,14 @@ def test_golden_aatgg_repeat():
         keys, counts, nv = oracle.count(reads, offsets, k, canonical)
         assert np.array_equal(keys, wk) and np.array_equal(counts, wc), (canonical, k)
         assert nv == reads.size - k + 1
+
+
+@pytest.mark.parametrize("k,canonical,threads", [(31, True, 4), (63, True, 3), (21, False, 7), (5, True, 16)])
+def test_parallel_variant_equals_the_oracle(k, canonical, threads):
+    """The multi-threaded variant (read ranges counted apart, merged by key with addition)
+    gives exactly the single-threaded oracle's histogram."""
+    reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.02)
+    want = oracle.count(reads, offsets, k, canonical)
+    got = oracle.count_parallel(reads, offsets, k, canonical, threads)
+    assert got[2] == want[2]
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
