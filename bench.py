@@ -33,19 +33,21 @@ WORKLOAD_DESC = {
     "repeats_100mbp_150bp_30x_k31": "100 Mbp genome (20% from 500 repeat families, Zipf 1.2, 2% divergence), "
                                     "150 bp reads, 30x, 0.5% subst, k=31 canonical",
     "long_50mbp_10kbp_20x_k63": "50 Mbp i.i.d. genome, log-normal 10 kbp reads, 20x, 5% errors 60/20/20, k=63 canonical",
-    "batch_256_samples_k31": "256 samples: i.i.d. genomes log-uniform 0.1-50 Mbp (times --scale, default 0.1), "
-                             "150 bp reads, U(5,40)x, 0.5% subst, k=31 canonical; kc_count_batch vs the per-sample "
-                             "kc_count loop",
+    "batch_256_samples_k31": "256 samples: i.i.d. genomes log-uniform 0.1-50 Mbp (times --scale), 150 bp reads, "
+                             "U(5,40)x, 0.5% subst, k=31 canonical (about 46 G bases); kc_count_batch in chunks "
+                             "against the per-sample kc_count loop, plan options per sample-size class from the "
+                             "autotuner",
 }
 BATCH_SEED = 1004  # seeds of the batched workload's samples: mix_seed(1004, i)
 WORKLOAD_DESC["serve_2000_requests"] = (
     "2000 count requests, Poisson arrivals at 200/s, k uniform in {21, 31, 63}, read sets of genomes log-uniform "
     "0.05-20 Mbp (times --scale), 150 bp reads, U(10,30)x, 0.5% subst (drawn from a pool of 32 generated read sets); "
-    "served by one plan: requests taken shortest expected first with ageing (kc_submit, queued on the plan's "
-    "stream, two submissions in flight) within a device-memory budget, completions polled (kc_job_poll), results "
-    "kept on the device; vs the same with continuous batching (waiting requests of the same k and similar size "
-    "submitted together as batched launches, kc_submit_batch), in arrival order, rounds of kc_count_batch, and one "
-    "kc_count per request")
+    "served by one plan: requests admitted while free device memory covers their footprint (kc_footprint), taken "
+    "shortest expected first with ageing (kc_submit, queued on the plan's stream, two submissions in flight), "
+    "completions polled (kc_job_poll), results handed to the client on the device; with continuous batching "
+    "(waiting requests of the same k and similar size submitted together as batched launches, kc_submit_batch); "
+    "against arrival order, rounds of kc_count_batch and one kc_count per request; latency at 200/s, throughput "
+    "with all requests at once")
 SERVE_SEED = 1005  # seeds of the served workload: pool read sets mix_seed(1005, i), arrivals RandomState(1005)
 
 
@@ -232,28 +234,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, with_cpu=True):
+    """Time one workload on this rank: the timed steps on a plain plan (CUDA events on its
+    stream), the per-kernel split from a separate profiled pass, the end-to-end figure
+    through the public API with host buffers, and (rank 0) the CPU baseline.  Returns the
+    JSON line's fields on rank 0, None elsewhere."""
     import torch
     import synth
     from paper_2505_04431_gb300 import KmerCounter
-    from paper_2505_04431_gb300 import build as kcbuild
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.cuda.current_device()
-    if rank == 0:
-        kcbuild.build()
-    if dist:
-        dist.barrier()
-    reads, offsets, k = synth.workload(args.workload, args.scale)
+    reads, offsets, k = synth.workload(workload, args.scale)
     n_reads, L = len(offsets) - 1, len(reads)
     stream = torch.cuda.Stream(dev)
     counter = KmerCounter(device=dev, stream=stream)  # the product path: no per-launch events
@@ -305,13 +295,14 @@ def run_ours(args):
     ms_per_step = elapsed_ms / args.steps
     value = whole_job_rate(K, world, args.steps, elapsed_ms)
 
-    # end to end through the public API with host buffers: pinned H2D inside the call, D2H of the result
+    # end to end through the public API with host buffers: pinned H2D inside the call, D2H of
+    # the result; its parts timed apart (CUDA events on the plan's stream)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e and not args.no_e2e:
         r_pin = torch.from_numpy(reads).pin_memory()
         o_pin = torch.from_numpy(offsets.view(np.int64)).pin_memory()
-        keys_h = torch.empty(D * kw, dtype=torch.int64).pin_memory()
-        cnt_h = torch.empty(D, dtype=torch.int32).pin_memory()
+        keys_h = torch.empty(max(1, D * kw), dtype=torch.int64).pin_memory()
+        cnt_h = torch.empty(max(1, D), dtype=torch.int32).pin_memory()
         import ctypes
         from paper_2505_04431_gb300 import load_library, _check
         lib = load_library()
@@ -332,14 +323,34 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        # the parts: reads and offsets in (the same pinned buffers), the count on device
+        # input, the result out, each with events on the plan's stream
+        rd = torch.empty_like(r_pin, device=dev)
+        od = torch.empty_like(o_pin, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            rd.copy_(r_pin, non_blocking=True)
+            od.copy_(o_pin, non_blocking=True)
+            e[1].record(stream)
+        res = counter.count(rd, od, k, True)
+        e[2].record(stream)
+        _check(lib, lib.kc_result_copy_to_host(counter._plan, ctypes.byref(res._res), keys_h.data_ptr(),
+                                               cnt_h.data_ptr()))
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        res.free()
+        parts = {"h2d_ms": e[0].elapsed_time(e[1]), "count_ms": e[1].elapsed_time(e[2]),
+                 "d2h_ms": e[2].elapsed_time(e[3])}
+        parts["host_ms"] = dt * 1e3 / e2e_steps - sum(parts.values())
+        del rd, od
         e2e = {"value": whole_job_rate(K, world, e2e_steps, dt * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(L + 8 * (n_reads + 1)), "d2h_bytes_per_step": int(D * (8 * kw + 4)),
-               "steps": e2e_steps}
+               "steps": e2e_steps, "ms_per_step": dt * 1e3 / e2e_steps, "parts": parts}
 
+    counter.close()
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
+        return None
     w = 8 * kw
     peak, peak_kind = measured_peaks()
     kb = kernel_bytes(L, n_reads, K, D, w)
@@ -349,14 +360,14 @@ def run_ours(args):
     achieved = kb[dom] / (avg[dom] / 1e3) / 1e9
     B = L + 8 * n_reads + 2 * K * w + D * (w + 4)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dom, args.workload),
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dom, workload),
                 "alg_bytes_per_launch": kb[dom], "ms_per_launch": avg[dom], "share": avg[dom] / total_k,
                 "timing": f"CUDA events on the plan's stream around every launch, {prof_steps} profiled steps"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64" if kw == 1 else "u128", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""), "k": k, "canonical": True,
+        "config": {"workload": workload, "desc": WORKLOAD_DESC.get(workload, ""), "k": k, "canonical": True,
                    "reads": n_reads, "bases": L, "windows": K, "distinct": D,
                    "l2": f"inputs larger than L2 ({L / 1e9:.2f} GB of reads, {K * w / 1e9:.1f} GB of keys per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
@@ -370,70 +381,145 @@ def run_ours(args):
         "e2e": e2e,
         "wall_s": wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and with_cpu and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(reads, offsets, k)
-    print(json.dumps(line), flush=True)
-    counter.close()
+    return line
+
+
+def run_ours(args):
+    import torch
+    from paper_2505_04431_gb300 import build as kcbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        kcbuild.build()
+    if dist:
+        dist.barrier()
+    line = measure(args.workload, args, dist, world, rank, dev)
     if dist:
         dist.destroy_process_group()
+    if rank != 0:
+        return
+    # the other forms, as extra keys of the same line (one GPU; each after the device memory
+    # of the one before is released)
+    if world == 1 and not args.no_extras and args.workload == DEFAULT_WORKLOAD:
+        extras = {}
+        for key, fn in (("long_50mbp_10kbp_20x_k63",
+                         lambda: measure("long_50mbp_10kbp_20x_k63", args, dev=dev, with_cpu=False)),
+                        ("batched", lambda: run_batch(args, as_summary=True)),
+                        ("served", lambda: run_serve(args, as_summary=True))):
+            torch.cuda.empty_cache()
+            t0 = time.perf_counter()
+            try:
+                extras[key] = fn()
+                extras[key]["seconds"] = time.perf_counter() - t0
+            except Exception as exc:  # recorded, so that the headline line is still printed
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        k63 = extras.get("long_50mbp_10kbp_20x_k63", {})
+        if "value" in k63:
+            extras["long_50mbp_10kbp_20x_k63"] = {
+                kk: k63[kk] for kk in ("value", "unit", "ms_per_step", "roofline", "path_roofline", "kernels_ms",
+                                       "e2e", "config", "clocks", "seconds") if kk in k63}
+        line["other_workloads"] = extras
+    print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
-    """The batched form against the plain per-sample loop, both timed end to end on the host
-    (wall clock around all calls, inputs resident on the device, results freed)."""
+def run_batch(args, as_summary=False):
+    """The batched form against the plain per-sample loop on the 256 samples of the batched
+    workload (genomes log-uniform 0.1-50 Mbp at 5-40x, about 46 G bases at --scale 1),
+    streamed through the GPU in chunks of samples whose results fit device memory, both
+    timed end to end on the host (wall clock around all calls, inputs resident on the
+    device, results freed as each chunk is done).  Plan options per sample-size class come
+    from the autotuner; untimed, every sample's result from the batch is compared on the
+    device, key for key and count for count, with its count alone."""
+    import concurrent.futures as cf
     import torch
     import synth
     from paper_2505_04431_gb300 import KmerCounter
     from paper_2505_04431_gb300 import build as kcbuild
+    from paper_2505_04431_gb300 import tune
 
     torch.cuda.set_device(0)
     kcbuild.build()
-    scale = 0.1 if args.scale == 1.0 else args.scale
-    samples, windows = [], 0
-    for i in range(256):
-        reads, offsets, _ = synth.generate(synth.SAMPLE, synth.mix_seed(BATCH_SEED, i), scale)
-        samples.append((torch.from_numpy(reads).cuda(), offsets, int(offsets[-1])))
-        windows += max(0, int(np.sum(np.maximum(np.diff(offsets.astype(np.int64)) - 30, 0))))
-    counter = KmerCounter()
-    t_plain, t_batch, valid = [], [], 0
+    scale = args.scale
+    samples = []
+    with cf.ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as ex:
+        for r, o, _ in ex.map(lambda i: synth.generate(synth.SAMPLE, synth.mix_seed(BATCH_SEED, i), scale), range(256)):
+            samples.append((torch.from_numpy(r).cuda(), torch.from_numpy(o.view(np.int64)).cuda(), int(o[-1])))
+    torch.cuda.synchronize()
+    bases = sum(s_[2] for s_ in samples)
+    # size classes, each with the plan options the autotuner picks on its median sample
+    cuts = (1 << 26, 1 << 29)  # 64 Mi, 512 Mi bases
+    cls = [sum(s_[2] >= c for c in cuts) for s_ in samples]
+    tuned, counters = {}, {}
+    for c in sorted(set(cls)):
+        members = sorted((i for i in range(len(samples)) if cls[i] == c), key=lambda i: samples[i][2])
+        med = samples[members[len(members) // 2]]
+        t = tune.autotune(med[0], med[1], 31, True, repeats=2)
+        tuned[c] = {"options": t["best"], "best_ms": t["best_ms"], "samples": len(members),
+                    "tuned_on_bases": med[2]}
+        counters[c] = KmerCounter(**t["best"])
+    # chunks of consecutive samples of one class whose result buffers stay within a budget
+    budget = 48 << 30
+    order = sorted(range(len(samples)), key=lambda i: (cls[i], samples[i][2]))
+    chunks, cur, used = [], [], 0
+    for i in order:
+        need = samples[i][2] * 12
+        if cur and (used + need > budget or cls[cur[0]] != cls[i]):
+            chunks.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += need
+    if cur:
+        chunks.append(cur)
 
-    from paper_2505_04431_gb300 import serve as sv
+    def batched(check=False):
+        v, bad = 0, []
+        for ch in chunks:
+            c = counters[cls[ch[0]]]
+            out = c.count_batch([samples[i] for i in ch], 31, True)
+            v += sum(res.n_valid_windows for res in out)
+            for i, res in zip(ch, out):
+                if check:
+                    alone = c.count(samples[i][0], samples[i][1], 31, True)
+                    if not _same(res, (alone.keys_tensor(), alone.counts_tensor(), alone.n_valid_windows)):
+                        bad.append(i)
+                    alone.free()
+                res.free()
+        return v, bad
 
-    def plain(digests=None):
+    def plain():
         v = 0
-        for r, o, _ in samples:
-            res = counter.count(r, o, 31, True)
-            v += res.n_valid_windows
-            if digests is not None:
-                digests.append(sv.result_digest(res))
-            res.free()
+        for ch in chunks:
+            c = counters[cls[ch[0]]]
+            for i in ch:
+                res = c.count(samples[i][0], samples[i][1], 31, True)
+                v += res.n_valid_windows
+                res.free()
         return v
 
-    def batched(digests=None):
-        out = counter.count_batch(samples, 31, True)
-        v = sum(res.n_valid_windows for res in out)
-        if digests is not None:
-            digests.extend(sv.result_digest(res) for res in out)
-        for res in out:
-            res.free()
-        return v
-
-    # checked once (not timed): every sample's result (distinct keys, windows, sums of keys
-    # and counts) is the same from the batch as from kc_count alone
-    dp, db = [], []
-    plain(dp)
-    batched(db)
-    mism = [i for i, (a, b) in enumerate(zip(dp, db)) if a != b]
-    if mism:
-        raise RuntimeError(f"batched results differ from kc_count for {len(mism)} samples (first: {mism[0]})")
-    launches = counter.stats()["kernel_launches"]
+    # checked once (not timed): every sample's result from the batch equals its count alone
+    _, bad = batched(check=True)
+    if bad:
+        raise RuntimeError(f"batched results differ from kc_count alone for {len(bad)} samples (first: {bad[0]})")
+    t_plain, t_batch, valid = [], [], 0
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         v1 = plain()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        v2 = batched()
+        v2, _ = batched()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         if v1 != v2:
@@ -443,24 +529,72 @@ def run_batch(args):
             t_plain.append(t1 - t0)
             t_batch.append(t2 - t1)
     tp, tb = float(np.median(t_plain)), float(np.median(t_batch))
-    bases = sum(s[2] for s in samples)
+    launches = sum(c.stats()["kernel_launches"] for c in counters.values())
+    # small samples alone: 256 samples of about 0.4 M bases, where launches dominate
+    small = []
+    for i in range(256):
+        r, o, _ = synth.generate(synth.SAMPLE, synth.mix_seed(BATCH_SEED + 1, i), 0.002)
+        small.append((torch.from_numpy(r).cuda(), torch.from_numpy(o.view(np.int64)).cuda(), int(o[-1])))
+    c0 = KmerCounter()
+    sw = sum(s_[2] for s_ in small)
+
+    def small_runs():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v = 0
+        for s_ in small:
+            res = c0.count(s_[0], s_[1], 31, True)
+            v += res.n_valid_windows
+            res.free()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = c0.count_batch(small, 31, True)
+        w = sum(res.n_valid_windows for res in out)
+        for res in out:
+            res.free()
+        torch.cuda.synchronize()
+        return t1 - t0, time.perf_counter() - t1, v, w
+
+    small_runs()
+    sp, sb, sv_, sw_ = small_runs()
+    c0.close()
+    for c in counters.values():
+        c.close()
+    out = {"samples": len(samples), "genome_scale": scale, "bases": bases, "windows": valid, "chunks": len(chunks),
+           "batched": {"value": valid / tb / 1e9, "unit": UNIT, "ms_per_step": tb * 1e3},
+           "plain": {"value": valid / tp / 1e9, "unit": UNIT, "ms_per_step": tp * 1e3},
+           "batched_vs_plain": tp / tb, "size_classes": {str(k): v for k, v in tuned.items()},
+           "small_samples": {"samples": len(small), "bases": sw, "plain_ms": sp * 1e3, "batched_ms": sb * 1e3,
+                             "batched_vs_plain": sp / sb, "plain_launches": 13 * len(small)},
+           "results_identical": True, "gpu_launches": launches}
+    if as_summary:
+        return out
     line = {"metric": METRIC, "value": valid / tb / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "samples": len(samples),
-                       "genome_scale": scale, "bases": bases, "windows": valid, "k": 31, "canonical": True,
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "k": 31, "canonical": True,
                        "parallelism": "1 GPU", "timing": "host wall clock around all calls, median of steps"},
-            "plain": {"value": valid / tp / 1e9, "unit": UNIT, "ms_per_step": tp * 1e3},
-            "batched_vs_plain": tp / tb, "results_identical": True, "gpu_launches": launches,
-            "plain_gpu_launches": 13 * len(samples)}
+            "batch": out, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
-    counter.close()
 
 
-def run_serve(args):
-    """The served form (kc_submit / kc_job_poll, one host thread) against rounds of
-    kc_count_batch and against one kc_count per request, on the same arrival sequence;
-    every request's result digest must agree between the three."""
+def _device_copy(res):
+    """The used part of a result, copied into tensors of its own (kept while results come and go)."""
+    return res.keys_tensor().clone(), res.counts_tensor().clone(), res.n_valid_windows
+
+
+def _same(res, ref) -> bool:
+    """Every key and count of a result equals the reference's (compared on the device)."""
+    import torch
+    return (res.n_valid_windows == ref[2] and res.n == ref[1].shape[0]
+            and bool(torch.equal(res.keys_tensor(), ref[0])) and bool(torch.equal(res.counts_tensor(), ref[1])))
+
+
+def run_serve(args, as_summary=False):
+    """The served form against the plain loop on one arrival sequence of 2000 requests:
+    latency at 200 requests/s (Poisson), throughput with all requests arriving at once
+    (saturation), and, untimed, every request's result compared key for key and count for
+    count with the same count alone."""
     import torch
     import synth
     from paper_2505_04431_gb300 import KmerCounter
@@ -469,11 +603,11 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     kcbuild.build()
-    pool = []
-    for i in range(32):
-        reads, offsets, _ = synth.generate(synth.SERVE, synth.mix_seed(SERVE_SEED, i), args.scale)
-        pool.append((torch.from_numpy(reads).cuda(), torch.from_numpy(offsets.view(np.int64)).cuda(),
-                     int(offsets[-1])))
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as ex:
+        gen = list(ex.map(lambda i: synth.generate(synth.SERVE, synth.mix_seed(SERVE_SEED, i), args.scale), range(32)))
+    pool = [(torch.from_numpy(r).cuda(), torch.from_numpy(o.view(np.int64)).cuda(), int(o[-1])) for r, o, _ in gen]
+    del gen
     torch.cuda.synchronize()
     rng = np.random.RandomState(SERVE_SEED)
     n_req, rate = 2000, 200.0
@@ -481,83 +615,87 @@ def run_serve(args):
     ks = rng.choice([21, 31, 63], n_req)
     picks = rng.randint(0, len(pool), n_req)
 
-    def make():
-        return [sv.Request(float(a), pool[p][0], pool[p][1], pool[p][2], int(k)) for a, k, p in zip(arrivals, ks, picks)]
+    def make(at_once=False):
+        return [sv.Request(0.0 if at_once else float(a), pool[p][0], pool[p][1], pool[p][2], int(k))
+                for a, k, p in zip(arrivals, ks, picks)]
 
-    free, _ = torch.cuda.mem_get_info()
-    budget = int(min(64 << 30, max(4 << 30, free - (24 << 30))))
     counter = KmerCounter()
-    # warm-up: every k once, submitted and counted directly; the largest input at k = 63
-    # last, so that the plan's scratch has its final size before the timed runs
-    big = max(range(len(pool)), key=lambda i: pool[i][2])
-    for k in (21, 31, 63):
-        counter.count(pool[0][0], pool[0][1], k).free()
-        counter.wait(counter.submit(pool[0][0], pool[0][1], k, True, n_bases=pool[0][2])).free()
-    counter.count(pool[big][0], pool[big][1], 63).free()
-    # the result of every (read set, k) in the mix, counted alone
+    # the result of every (read set, k) of the mix, counted alone and kept on the device
     ref = {}
     for p_, k_ in sorted(set(zip(picks.tolist(), ks.tolist()))):
         res = counter.count(pool[p_][0], pool[p_][1], k_)
-        ref[(p_, k_)] = sv.result_digest(res)
+        ref[(p_, k_)] = _device_copy(res)
         res.free()
-    # timed: latency to the completion of each count (results stay on the device)
-    runs = {}
-    for name in ("served", "served_batched", "served_fifo", "batch_rounds", "plain"):
+    torch.cuda.synchronize()
+    free_result = lambda r, res: res.free()  # noqa: E731  (the client is done with it)
+    servers = {
+        "served": lambda reqs: sv.serve_async(counter, reqs, keep_digest=False, policy="sjf", on_result=free_result),
+        "served_batched": lambda reqs: sv.serve_async(counter, reqs, keep_digest=False, policy="sjf", batch=True,
+                                                      on_result=free_result),
+        "served_fifo": lambda reqs: sv.serve_async(counter, reqs, keep_digest=False, policy="fifo",
+                                                   on_result=free_result),
+        "batch_rounds": lambda reqs: sv.serve(counter, reqs, keep_digest=False, on_result=free_result),
+        "plain": lambda reqs: sv.serve_one_at_a_time(counter, reqs, keep_digest=False, on_result=free_result),
+    }
+    servers["served_batched"](make(True))  # warm-up: every k and size once, scratch grown
+    runs, sat = {}, {}
+    for name, fn in servers.items():
         reqs = make()
         torch.cuda.synchronize()
-        if name == "served":
-            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="sjf")
-        elif name == "served_batched":
-            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="sjf", batch=True)
-        elif name == "served_fifo":
-            info = sv.serve_async(counter, reqs, budget, keep_digest=False, policy="fifo")
-        elif name == "batch_rounds":
-            info = sv.serve(counter, reqs, budget, keep_digest=False)
-        else:
-            info = sv.serve_one_at_a_time(counter, reqs, keep_digest=False)
-        runs[name] = (reqs, info)
-    served = runs["served"][0]
+        runs[name] = (reqs, fn(reqs))
+    for name in ("served_batched", "served", "plain"):
+        reqs = make(True)
+        torch.cuda.synchronize()
+        sat[name] = (reqs, servers[name](reqs))
     # checked (not timed): every request's result in the mix equals the same count alone
+    checked = 0
     for name in ("served", "served_batched", "batch_rounds"):
-        reqs = make()
-        for r in reqs:
-            r.arrival = 0.0  # all at once: the longest queues
-        if name == "served":
-            sv.serve_async(counter, reqs, budget, policy="sjf")
-        elif name == "served_batched":
-            sv.serve_async(counter, reqs, budget, policy="sjf", batch=True)
+        bad = []
+
+        def check(r, res, bad=bad):
+            if not _same(res, ref[(r._pick, r.k)]):
+                bad.append(r)
+            res.free()
+
+        reqs = make(True)
+        for r, p_ in zip(reqs, picks):
+            r._pick = int(p_)
+        if name == "batch_rounds":
+            sv.serve(counter, reqs, keep_digest=False, on_result=check)
         else:
-            sv.serve(counter, reqs, budget)
-        mism = [i for i, (r, p_, k_) in enumerate(zip(reqs, picks, ks)) if r.digest != ref[(int(p_), int(k_))]]
-        if mism:
-            raise RuntimeError(f"{name}: results differ from single counts for {len(mism)} requests (first: {mism[0]})")
-    windows = sum(r.n_valid for r in served)
+            sv.serve_async(counter, reqs, keep_digest=False, policy="sjf", batch=name == "served_batched",
+                           on_result=check)
+        if bad:
+            raise RuntimeError(f"{name}: {len(bad)} results differ from the same count alone")
+        checked += len(reqs)
+    windows = sum(r.n_valid for r in runs["served"][0])
 
-    def summary(name):
-        reqs, info = runs[name]
+    def summary(reqs, info):
         return {"value": windows / info["makespan"] / 1e9, "unit": UNIT, "ms_per_step": info["makespan"] * 1e3,
-                "latency": sv.latency_summary(reqs)}
+                "latency": sv.latency_summary(reqs), "submissions": info["batches"]}
 
-    ls, lc, lf, lb, lp = (summary(n) for n in ("served", "served_batched", "served_fifo", "batch_rounds", "plain"))
-    line = {"metric": METRIC, "value": ls["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-            "warmup": 1, "ms_per_step": ls["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64/u128", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "requests": n_req,
-                       "rate_per_s": rate, "genome_scale": args.scale, "windows": windows,
-                       "offered_gkmers_per_s": windows / float(arrivals[-1]) / 1e9,
-                       "budget_gb": budget / 2**30, "parallelism": "1 GPU",
-                       "timing": "host wall clock; latency = arrival to the host seeing the count complete"},
-            "latency": ls["latency"], "peak_inflight": runs["served"][1]["peak_inflight"],
-            "policy": "shortest expected service first, with ageing; 2 submissions queued on the GPU",
-            "served_batched": dict(lc, policy="the same, and the waiting requests of the same k and similar size "
-                                              "in one submission of batched launches (continuous batching)",
-                                   submissions=runs["served_batched"][1]["batches"]),
-            "served_fifo": lf, "batch_rounds": lb, "plain": lp,
-            "p50_plain_over_served": lp["latency"]["p50_ms"] / ls["latency"]["p50_ms"],
-            "p99_plain_over_served": lp["latency"]["p99_ms"] / ls["latency"]["p99_ms"],
-            "results_identical": True, "gpu_launches": 13 * n_req}
-    print(json.dumps(line), flush=True)
+    lat = {n: summary(*runs[n]) for n in runs}
+    thr = {n: summary(*sat[n]) for n in sat}
+    out = {"requests": n_req, "rate_per_s": rate, "windows": windows,
+           "offered_gkmers_per_s": windows / float(arrivals[-1]) / 1e9,
+           "at_200_per_s": {n: {"p50_ms": v["latency"]["p50_ms"], "p99_ms": v["latency"]["p99_ms"],
+                                "gkmers_per_s": v["value"], "submissions": v["submissions"]} for n, v in lat.items()},
+           "saturated": {n: {"gkmers_per_s": v["value"], "makespan_ms": v["ms_per_step"],
+                             "submissions": v["submissions"]} for n, v in thr.items()},
+           "served_over_plain_saturated": thr["served_batched"]["value"] / thr["plain"]["value"],
+           "results_checked": checked, "results_identical": True}
     counter.close()
+    if as_summary:
+        return out
+    line = {"metric": METRIC, "value": thr["served_batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": thr["served_batched"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64/u128", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload], "genome_scale": args.scale,
+                       "parallelism": "1 GPU",
+                       "timing": "host wall clock; latency = arrival to the host seeing the count complete; value = "
+                                 "windows / makespan with all 2000 requests arriving at once"},
+            "served": out, "gpu_launches": 13 * n_req}
+    print(json.dumps(line), flush=True)
 
 
 WORKLOAD_DESC["ablation_aggregation"] = (
@@ -639,6 +777,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the headline workload only (no k=63, batched and served summaries)")
     ap.add_argument("--scale", type=float, default=1.0, help="genome scale (diagnostics only; 1.0 = the workload)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

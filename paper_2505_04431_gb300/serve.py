@@ -1,17 +1,24 @@
 """Served form: request loops over the k-mer counter.
 
 Count requests (a read set and k) arrive over time; each request's latency runs from its
-arrival to the moment its result is complete on the device.  Two servers:
+arrival to the moment its result is complete on the device.  Servers:
 
-- serve_async (the served form): every arrived request whose device footprint fits what
-  is left of the memory budget is submitted at once (kc_submit) and queued on the plan's
-  stream, its scratch kept on the device; results are collected as they complete
-  (kc_job_poll), so the GPU runs the requests back to back with no host round trip
-  between them, and the host prepares and checks requests while the GPU counts.
+- serve_async (the served form): arrived requests are admitted while the device's free
+  memory covers what they take (kc_footprint: their result buffers and the scratch they
+  need), submitted at once (kc_submit) and queued on the plan's stream; results are
+  collected as they complete (kc_job_poll), so the GPU runs the requests back to back
+  with no host round trip between them, and the host prepares and checks requests while
+  the GPU counts.  With continuous batching, waiting requests of one k go together in one
+  submission of batched launches (kc_submit_batch): their thread blocks share every
+  kernel launch, so their work overlaps on the device.
 - serve: rounds of kc_count_batch over the requests that arrived meanwhile (one call per
   k), for bursts of many requests.
+- serve_one_at_a_time: the plain loop, one kc_count per request.
 
-No part of the counting happens here: this module only orders calls into the library.
+Every server hands each result to on_result(request, result) as soon as it is complete;
+by default the result stays on the device in request.result until the caller frees it
+(result.free()).  No part of the counting happens here: this module only orders calls
+into the library.
 """
 from __future__ import annotations
 
@@ -20,10 +27,6 @@ import dataclasses
 import time
 
 import numpy as np
-
-# device bytes per base a count needs at most: two key buffers of 8 or 16 bytes, the packed
-# reads, the result buffers (keys + counts) and small per-tile / per-partition arrays
-FOOTPRINT_PER_BASE = {1: 2 * 8 + 8 + 4 + 2, 2: 2 * 16 + 16 + 4 + 2}
 
 
 @dataclasses.dataclass
@@ -37,10 +40,28 @@ class Request:
     n_distinct: int = -1
     n_valid: int = -1
     digest: tuple = ()
+    result: object = None  # the result, kept on the device (default on_result)
 
 
-def footprint(req: Request) -> int:
-    return req.n_bases * FOOTPRINT_PER_BASE[1 if req.k <= 32 else 2] + (64 << 20)
+def _on_device(x) -> bool:
+    return bool(getattr(x, "is_cuda", False))
+
+
+def footprint(counter, req: Request) -> int:
+    """Device bytes the request takes while it is in flight: the scratch its count needs
+    and its result buffers (kc_footprint on the counter's plan)."""
+    n_reads = (req.offsets.shape[0] if hasattr(req.offsets, "shape") else len(req.offsets)) - 1
+    on_dev = _on_device(req.reads) and (req.reads.data_ptr() % 16 == 0)
+    scratch, result = counter.footprint(n_reads, req.n_bases, req.k, on_dev, _on_device(req.offsets))
+    return scratch + result
+
+
+def device_free_bytes() -> int:
+    """Device memory a count can still get: what the driver reports free, plus what torch's
+    caching allocator holds without using it (the library allocates through it)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return int(free + torch.cuda.memory_reserved() - torch.cuda.memory_allocated())
 
 
 def result_digest(res):
@@ -54,12 +75,16 @@ def result_digest(res):
     return (res.n, res.n_valid_windows, h.hexdigest())
 
 
-def _finish(r: Request, res, t_done: float, keep_digest: bool):
+def keep_result(r: Request, res):
+    r.result = res
+
+
+def _finish(r: Request, res, t_done: float, keep_digest: bool, on_result):
     r.done = t_done
     r.n_distinct, r.n_valid = res.n, res.n_valid_windows
-    if keep_digest:  # on the current stream: behind any counts still queued there
+    if keep_digest:
         r.digest = result_digest(res)
-    res.free()
+    (on_result or keep_result)(r, res)
 
 
 # service time a count is expected to take (ordering only): per base, by key width, plus a
@@ -72,30 +97,52 @@ def expected_seconds(req: Request) -> float:
     return SECONDS_FIXED + req.n_bases * SECONDS_PER_BASE[1 if req.k <= 32 else 2]
 
 
-def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: bool = True,
-                keep_digest: bool = True, idle_sleep: float = 50e-6, policy: str = "fifo", depth: int | None = None,
-                batch: bool = False, max_batch: int = 64, batch_ratio: float = 4.0):
-    """Submit arrived requests while the footprints of the requests in flight stay within the
-    budget (and, with `depth`, while fewer than `depth` submissions are in flight); collect
-    results as they complete.  One request is always admitted when none is in flight,
-    whatever its footprint.  policy "fifo" takes the waiting requests in arrival order;
-    "sjf" takes next the one with the least expected service time minus the time it has
-    waited (shortest first, with ageing so that a large request is not held back for ever),
-    and defaults to depth 2, so that the GPU always has the next submission queued.  With
-    `batch` (continuous batching), the waiting requests with the same k whose expected
-    service time is at most `batch_ratio` times that of the request taken (or under 1 ms)
-    join it, in policy order and within the budget, in one submission of batched launches
-    (kc_submit_batch, at most `max_batch` requests)."""
+class _Admission:
+    """Admits work while free device memory (less `headroom`) covers it, and, with a budget,
+    while the footprints in flight stay within it.  One request is always admitted when
+    nothing is in flight, whatever it takes."""
+
+    def __init__(self, counter, mem_free, headroom, budget_bytes):
+        self.counter = counter
+        self.mem_free = mem_free or device_free_bytes
+        self.headroom = headroom
+        self.budget = budget_bytes
+        self.used = 0
+
+    def fits(self, need: int, idle: bool) -> bool:
+        if idle:
+            return True
+        if self.budget is not None and self.used + need > self.budget:
+            return False
+        return need <= self.mem_free() - self.headroom
+
+
+def serve_async(counter, requests: list[Request], canonical: bool = True, keep_digest: bool = True,
+                idle_sleep: float = 50e-6, policy: str = "fifo", depth: int | None = None, batch: bool = False,
+                max_batch: int = 64, batch_ratio: float = 4.0, on_result=None, mem_free=None,
+                headroom: int = 1 << 30, budget_bytes: int | None = None):
+    """Submit arrived requests while free device memory covers their footprints (and, with
+    `depth`, while fewer than `depth` submissions are in flight); collect results as they
+    complete.  policy "fifo" takes the waiting requests in arrival order; "sjf" takes next
+    the one with the least expected service time minus the time it has waited (shortest
+    first, with ageing so that a large request is not held back for ever), and defaults to
+    depth 2, so that the GPU always has the next submission queued.  With `batch`
+    (continuous batching), the waiting requests with the same k whose expected service time
+    is at most `batch_ratio` times that of the request taken (or under 1 ms) join it, in
+    policy order and while memory covers them, in one submission of batched launches
+    (kc_submit_batch, at most `max_batch` requests).  mem_free() gives the free device
+    bytes (default device_free_bytes); budget_bytes optionally caps the footprints in
+    flight as well."""
     if policy not in ("fifo", "sjf"):
         raise ValueError(f"unknown policy {policy!r}")
     if depth is None and policy == "sjf":
         depth = 2
+    adm = _Admission(counter, mem_free, headroom, budget_bytes)
     queue = collections.deque(sorted(requests, key=lambda r: r.arrival))
     waiting: list = []
     inflight: dict = {}  # job id -> (request, footprint, submission)
     open_subs: dict = {}  # submission -> its jobs still in flight
     next_sub = 0
-    used = 0
     peak_inflight = 0
     submissions = 0
     t0 = time.perf_counter()
@@ -110,30 +157,33 @@ def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: 
                 prio = lambda q: q  # noqa: E731
             i = min(range(len(waiting)), key=prio)
             r = waiting[i]
-            f = footprint(r)
-            if inflight and used + f > budget_bytes:
+            f = footprint(counter, r)
+            if not adm.fits(f, not inflight):
                 break
-            group, tot = [i], used + f
+            group, need, feet = [i], f, {i: f}
             if batch:
                 cap = max(batch_ratio * expected_seconds(r), 1e-3)
                 for q in sorted((q for q in range(len(waiting)) if q != i and waiting[q].k == r.k), key=prio):
                     if len(group) >= max_batch:
                         break
-                    fq = footprint(waiting[q])
-                    if expected_seconds(waiting[q]) <= cap and tot + fq <= budget_bytes:
+                    if expected_seconds(waiting[q]) > cap:
+                        continue
+                    fq = footprint(counter, waiting[q])
+                    if adm.fits(need + fq, False):
                         group.append(q)
-                        tot += fq
+                        need += fq
+                        feet[q] = fq
             reqs = [waiting[q] for q in group]
             if len(reqs) == 1:
                 jobs = [counter.submit(r.reads, r.offsets, r.k, canonical, n_bases=r.n_bases)]
             else:
                 jobs = counter.submit_batch([(x.reads, x.offsets, x.n_bases) for x in reqs], r.k, canonical)
             open_subs[next_sub] = len(jobs)
-            for job, x in zip(jobs, reqs):
-                inflight[job] = (x, footprint(x), next_sub)
+            for job, q in zip(jobs, group):
+                inflight[job] = (waiting[q], feet[q], next_sub)
             next_sub += 1
             submissions += 1
-            used = tot
+            adm.used += need
             for q in sorted(group, reverse=True):
                 waiting.pop(q)
         peak_inflight = max(peak_inflight, len(inflight))
@@ -143,11 +193,11 @@ def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: 
             if res is None:
                 continue
             r, f, sub = inflight.pop(job)
-            used -= f
+            adm.used -= f
             open_subs[sub] -= 1
             if not open_subs[sub]:
                 del open_subs[sub]
-            _finish(r, res, time.perf_counter() - t0, keep_digest)
+            _finish(r, res, time.perf_counter() - t0, keep_digest, on_result)
             progressed = True
         if not progressed:
             if not inflight and not waiting and queue:
@@ -157,8 +207,11 @@ def serve_async(counter, requests: list[Request], budget_bytes: int, canonical: 
     return {"batches": submissions, "peak_inflight": peak_inflight, "makespan": time.perf_counter() - t0}
 
 
-def serve(counter, requests: list[Request], budget_bytes: int, canonical: bool = True, keep_digest: bool = True):
-    """Continuous batching in arrival order; fills done / n_distinct / n_valid / digest."""
+def serve(counter, requests: list[Request], canonical: bool = True, keep_digest: bool = True, on_result=None,
+          mem_free=None, headroom: int = 1 << 30, budget_bytes: int | None = None):
+    """Rounds of kc_count_batch in arrival order: each round takes the arrived requests
+    that free device memory covers (at least one), one call per k."""
+    adm = _Admission(counter, mem_free, headroom, budget_bytes)
     queue = collections.deque(sorted(requests, key=lambda r: r.arrival))
     waiting: list[Request] = []
     t0 = time.perf_counter()
@@ -170,14 +223,14 @@ def serve(counter, requests: list[Request], budget_bytes: int, canonical: bool =
         if not waiting:
             time.sleep(max(0.0, min(queue[0].arrival - now, 0.002)))
             continue
-        # admit in arrival order while the budget holds (at least one request per round)
-        admitted, used = [], 0
+        # admit in arrival order while memory holds (at least one request per round)
+        admitted, need = [], 0
         for r in waiting:
-            f = footprint(r)
-            if admitted and used + f > budget_bytes:
+            f = footprint(counter, r)
+            if admitted and not adm.fits(need + f, False):
                 continue
             admitted.append(r)
-            used += f
+            need += f
         admitted_ids = {id(r) for r in admitted}
         waiting = [r for r in waiting if id(r) not in admitted_ids]
         by_k = collections.defaultdict(list)
@@ -187,12 +240,13 @@ def serve(counter, requests: list[Request], budget_bytes: int, canonical: bool =
             results = counter.count_batch([(r.reads, r.offsets, r.n_bases) for r in group], k, canonical)
             t_done = time.perf_counter() - t0
             for r, res in zip(group, results):
-                _finish(r, res, t_done, keep_digest)
+                _finish(r, res, t_done, keep_digest, on_result)
             batches += 1
     return {"batches": batches, "makespan": time.perf_counter() - t0}
 
 
-def serve_one_at_a_time(counter, requests: list[Request], canonical: bool = True, keep_digest: bool = True):
+def serve_one_at_a_time(counter, requests: list[Request], canonical: bool = True, keep_digest: bool = True,
+                        on_result=None):
     """The plain loop: one kc_count per request, first come first served."""
     queue = sorted(requests, key=lambda r: r.arrival)
     t0 = time.perf_counter()
@@ -201,7 +255,7 @@ def serve_one_at_a_time(counter, requests: list[Request], canonical: bool = True
         if r.arrival > now:
             time.sleep(r.arrival - now)
         res = counter.count(r.reads, r.offsets, r.k, canonical)
-        _finish(r, res, time.perf_counter() - t0, keep_digest)
+        _finish(r, res, time.perf_counter() - t0, keep_digest, on_result)
     return {"batches": len(queue), "makespan": time.perf_counter() - t0}
 
 

@@ -3,8 +3,8 @@
 For a representative input, kc_count is timed (CUDA events on the plan's stream) under a
 few plan options: the coarse partition count the library picks by itself, half and twice
 that count, then the table load at the best count.  Every candidate must return the same
-result (distinct keys, windows, sums of keys and counts), and the fastest options are
-returned for use with KmerCounter(**options) or count_batch on inputs of the same kind.
+result (every key and count, compared on the device), and the fastest options are returned
+for use with KmerCounter(**options) or count_batch on inputs of the same kind.
 No part of the counting happens here: this module only times calls into the library.
 """
 from __future__ import annotations
@@ -13,15 +13,35 @@ MAX_PARTITIONS = 4096
 TABLE_LOADS = (0.45, 0.55)
 
 
+class _DeviceResult:
+    """A result's keys and counts, copied on the device; equal only if every key and count
+    is (compared on the device, so that large results need no trip to the host)."""
+
+    def __init__(self, res):
+        self.keys = res.keys_tensor().clone()
+        self.counts = res.counts_tensor().clone()
+        self.n_valid = res.n_valid_windows
+
+    def __eq__(self, other):
+        import torch
+        return (isinstance(other, _DeviceResult) and self.n_valid == other.n_valid
+                and self.keys.shape == other.keys.shape and bool(torch.equal(self.keys, other.keys))
+                and bool(torch.equal(self.counts, other.counts)))
+
+    def __ne__(self, other):
+        return not self.__eq__(other)
+
+
 def _time_count(make_counter, opts, reads, offsets, k, canonical, repeats):
-    """(median ms, digest, coarse partitions used) of kc_count under plan options `opts`."""
+    """(median ms, the result, coarse partitions used) of kc_count under plan options `opts`."""
     import torch
-    from .serve import result_digest
     stream = torch.cuda.Stream()
     counter = make_counter(stream=stream, **opts)
     try:
-        res = counter.count(reads, offsets, k, canonical)  # warm-up; its digest is the check
-        digest = result_digest(res)
+        res = counter.count(reads, offsets, k, canonical)  # warm-up; its result is the check
+        with torch.cuda.stream(stream):
+            digest = _DeviceResult(res)
+        stream.synchronize()
         res.free()
         p1 = counter.stats()["n_partitions"]
         times = []

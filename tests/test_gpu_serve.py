@@ -152,7 +152,7 @@ def digests_alone(counter, reqs):
 def test_served_async_results_identical_to_single_counts(counter, torch_cuda):
     from paper_2505_04431_gb300 import serve as sv
     reqs = make_requests(torch_cuda)
-    info = sv.serve_async(counter, reqs, budget_bytes=2 << 30)
+    info = sv.serve_async(counter, reqs, budget_bytes=2 << 30, on_result=lambda r, res: res.free())
     assert info["peak_inflight"] > 1  # requests were queued behind each other
     assert [r.digest for r in reqs] == digests_alone(counter, reqs)
     assert all(r.done >= r.arrival for r in reqs)
@@ -161,7 +161,7 @@ def test_served_async_results_identical_to_single_counts(counter, torch_cuda):
 def test_served_batches_identical_to_single_counts(counter, torch_cuda):
     from paper_2505_04431_gb300 import serve as sv
     reqs = make_requests(torch_cuda, seed=8)
-    info = sv.serve(counter, reqs, budget_bytes=2 << 30)
+    info = sv.serve(counter, reqs, budget_bytes=2 << 30, on_result=lambda r, res: res.free())
     assert info["batches"] < len(reqs)  # requests were batched
     assert [r.digest for r in reqs] == digests_alone(counter, reqs)
 
@@ -214,6 +214,7 @@ def test_submit_batch_matches_single_counts(counter, torch_cuda):
 def test_served_async_batched_identical_to_single_counts(counter, torch_cuda):
     from paper_2505_04431_gb300 import serve as sv
     reqs = make_requests(torch_cuda, n=60, seed=9)
-    info = sv.serve_async(counter, reqs, budget_bytes=2 << 30, policy="sjf", batch=True)
+    info = sv.serve_async(counter, reqs, budget_bytes=2 << 30, policy="sjf", batch=True,
+                          on_result=lambda r, res: res.free())
     assert info["batches"] < len(reqs)  # some requests shared a submission
     assert [r.digest for r in reqs] == digests_alone(counter, reqs)
