@@ -236,21 +236,23 @@ kc_status kc_count_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *cons
  * thread can keep many counts queued (for a service that takes requests as they arrive)
  * and the GPU runs them back to back, without a host round trip between two counts.
  *
- * kc_submit checks the arguments, sizes the count and enqueues its copies and kernels at
- * once on the plan's stream, behind the counts already queued there (the plan's scratch
- * grows in stream order when a count needs more), and returns without waiting for the
- * GPU.  Counts never run concurrently with each other on the device.
+ * kc_submit checks the arguments, sizes the count and enqueues its kernels at once on the
+ * plan's stream, behind the counts already queued there (the plan's scratch grows in
+ * stream order when a count needs more), and returns without waiting for the GPU.  Counts
+ * never run concurrently with each other on the device.  Inputs in host memory are copied
+ * into a device buffer of the job's own on the plan's transfer stream (a second stream the
+ * plan creates at its first submission), and the count's kernels wait for that copy: the
+ * copy of the next count's inputs runs while the counts before it are still counting.
  *   reads, offsets, n_reads   as for kc_count (host or device memory).  They are read
- *                  by the GPU after kc_submit returns: keep them valid and unchanged
- *                  until the job is collected.  Host buffers should be pinned
- *                  (cudaMallocHost / cudaHostRegister); copies from pageable memory
- *                  may make the call wait for earlier work.
+ *                  after kc_submit returns: keep them valid and unchanged until the job
+ *                  is collected.  Host buffers should be pinned (cudaMallocHost /
+ *                  cudaHostRegister); copies from pageable memory may make the call wait.
  *   n_bases        offsets[n_reads] (known to the caller, so nothing is read back).
  *   *job           a nonzero job id, valid until the job is collected.
  * At most 4096 jobs are in flight per plan (KC_EBUSY beyond).
- * Errors: KC_EINVAL (as for kc_count; host offsets are checked at once, device offsets
- * by the GPU, reported when the job is collected), KC_ENOMEM, KC_ECUDA; no job is
- * created then.
+ * Errors: KC_EINVAL (as for kc_count; for host offsets offsets[0] = 0 and
+ * offsets[n_reads] = n_bases are checked at once, the order of all offsets by the GPU and
+ * reported when the job is collected), KC_ENOMEM, KC_ECUDA; no job is created then.
  *
  * kc_job_poll collects a job if it has finished: *done = 0 while it runs (KC_OK, *out
  * zeroed); once finished *done = 1 and *out holds the result exactly as kc_count returns
@@ -272,6 +274,24 @@ kc_status kc_submit_batch(kc_plan_t plan, uint32_t n_samples, const uint8_t *con
                           const uint64_t *const *offsets, const uint64_t *n_reads, const uint64_t *n_bases, int k,
                           int canonical, uint64_t *job_ids);
 kc_status kc_job_wait(kc_plan_t plan, uint64_t job, kc_result *out);
+
+/* Result of a submitted count copied to host memory as soon as the count ends, so that
+ * the copy runs while the counts queued after it count (the pipelined form of kc_count +
+ * kc_result_copy_to_host for a stream of inputs).  Call it after kc_submit /
+ * kc_submit_batch and before the job is collected.  When the host sees the count end
+ * (kc_job_poll / kc_job_wait), the result's keys and counts (out->n entries, laid out as
+ * in kc_result) are copied on the plan's transfer stream to keys_host / counts_host, and
+ * the job is reported done only once that copy has completed; the device result is still
+ * returned and must still be freed with kc_free.
+ *   keys_host      capacity * key_words uint64 words; counts_host: capacity uint32 (host
+ *                  memory, pinned for the copy to overlap; device pointers also work).
+ *                  Both must stay valid until the job is collected.
+ *   capacity       entries the buffers hold; a result with more distinct keys fails the
+ *                  job with KC_EINVAL when it is collected (its buffers are released).
+ * Errors: KC_EINVAL (NULL arguments, unknown job, copy already under way), KC_EBUSY,
+ * KC_ECUDA. */
+kc_status kc_job_copy_to_host(kc_plan_t plan, uint64_t job, uint64_t *keys_host, uint32_t *counts_host,
+                              uint64_t capacity);
 
 #ifdef __cplusplus
 }

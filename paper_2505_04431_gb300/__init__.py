@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "K
 # every entry point declared in include/kc.h
 EXPORTED = ["kc_plan", "kc_count", "kc_free", "kc_result_copy_to_host", "kc_plan_destroy",
             "kc_last_error", "kc_last_stats", "kc_last_kernel_times", "kc_count_noalloc", "kc_count_batch",
-            "kc_submit", "kc_job_poll", "kc_job_wait", "kc_submit_batch", "kc_footprint"]
+            "kc_submit", "kc_job_poll", "kc_job_wait", "kc_submit_batch", "kc_footprint",
+            "kc_job_copy_to_host"]
 KC_NOALLOC_MAX_BASES = 1 << 20
 KC_PLAN_PROFILE = 1
 KC_PLAN_DEFER_ALL = 2
@@ -113,6 +114,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.kc_submit_batch.restype = i32
     lib.kc_footprint.argtypes = [vp, u64, u64, i32, i32, i32, P(u64), P(u64)]
     lib.kc_footprint.restype = i32
+    lib.kc_job_copy_to_host.argtypes = [vp, u64, vp, vp, u64]
+    lib.kc_job_copy_to_host.restype = i32
     _lib = lib
     return lib
 
@@ -339,6 +342,21 @@ class KmerCounter:
         for j, kept in zip(out, keep):
             self._inflight[j] = kept
         return out
+
+    def copy_to_host(self, job: int, keys_host, counts_host) -> None:
+        """Have a submitted job's result copied to host buffers as soon as its count ends
+        (kc_job_copy_to_host): keys_host holds capacity x key words (int64/uint64), counts_host
+        capacity counts (int32/uint32); pinned memory lets the copy overlap later counts.
+        The job is reported done once the copy has completed."""
+        for x in (keys_host, counts_host):
+            ok = x.flags["C_CONTIGUOUS"] if isinstance(x, np.ndarray) else x.is_contiguous()
+            if not ok:
+                raise ValueError("copy_to_host: the host buffers must be contiguous")
+        kp, kk = _ptr(keys_host)
+        cp, ck = _ptr(counts_host)
+        cap = counts_host.shape[0] if hasattr(counts_host, "shape") else len(counts_host)
+        _check(self._lib, self._lib.kc_job_copy_to_host(self._plan, int(job), kp, cp, int(cap)))
+        self._inflight[int(job)] = self._inflight.get(int(job), ()) + (kk, ck)
 
     def poll(self, job: int) -> CountResult | None:
         """The job's result if it has finished (kc_job_poll), else None."""

@@ -194,6 +194,9 @@ struct kc_plan_s {
   int stg_next = 0;
   // submitted counts (kc_submit): jobs in flight and their pinned status records
   std::unordered_map<uint64_t, AsyncJob*> jobs;
+  // transfer stream of submitted counts: host inputs in, results out to host buffers, so
+  // that these copies overlap the counts queued before and after them on `stream`
+  cudaStream_t xfer = nullptr;
   uint64_t next_job = 1;
   static constexpr int kPinned = 4096;
   struct kc::Meta* pinned = nullptr;
@@ -217,21 +220,26 @@ struct kc_plan_s {
 
 namespace {
 
-void* dev_alloc(kc_plan_s* p, size_t bytes) {
+// Device memory for use on stream `st` (the plan's stream unless stated): a block is only
+// ever written by work on the stream it was allocated for, or by work ordered after that
+// stream's use of it, and it is freed on that stream once the host has seen that work end.
+void* dev_alloc_on(kc_plan_s* p, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 256;
-  if (p->alloc) return p->alloc(bytes, (void*)p->stream, p->ctx);
+  if (p->alloc) return p->alloc(bytes, (void*)st, p->ctx);
   void* ptr = nullptr;
-  if (cudaMallocAsync(&ptr, bytes, p->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&ptr, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   return ptr;
 }
-void dev_free(kc_plan_s* p, void* ptr) {
+void dev_free_on(kc_plan_s* p, void* ptr, cudaStream_t st) {
   if (!ptr) return;
-  if (p->free_) p->free_(ptr, (void*)p->stream, p->ctx);
-  else cudaFreeAsync(ptr, p->stream);
+  if (p->free_) p->free_(ptr, (void*)st, p->ctx);
+  else cudaFreeAsync(ptr, st);
 }
+void* dev_alloc(kc_plan_s* p, size_t bytes) { return dev_alloc_on(p, bytes, p->stream); }
+void dev_free(kc_plan_s* p, void* ptr) { dev_free_on(p, ptr, p->stream); }
 
 bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes a;
@@ -280,8 +288,13 @@ struct Job {
   uint32_t nf_max = 0;
   uint64_t L = 0, n_reads = 0;
   bool off_dev = false, copy_reads = false, reads_dev = false;
+  // host inputs of a submitted count, copied on the transfer stream into a buffer of the
+  // job's own (not the plan's scratch) so that the copy may run while earlier counts do
+  bool stage_r = false, stage_o = false;
   const uint8_t* reads = nullptr;
   const uint64_t* offsets = nullptr;
+  const uint8_t* stage_reads = nullptr;
+  const uint64_t* stage_offs = nullptr;
   size_t ws_bytes = 0, out_key_bytes = 0, out_cnt_bytes = 0;
   void* okeys = nullptr;
   void* ocnts = nullptr;
@@ -303,7 +316,7 @@ kc::ShapeOpts shape_opts(const kc_plan_s* p) {
 }
 
 void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t L,
-              bool off_dev, int k, int canonical, Job& j) {
+              bool off_dev, int k, int canonical, Job& j, bool stage_host = false) {
   j.reads = reads;
   j.offsets = offsets;
   j.n_reads = n_reads;
@@ -311,7 +324,10 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   j.off_dev = off_dev;
   j.reads_dev = L > 0 && is_device_ptr(reads);
   j.copy_reads = L > 0 && (!j.reads_dev || ((uintptr_t)reads & 15) != 0);
-  j.nf_max = kc::make_shape(shape_opts(p), L, n_reads, k, canonical, j.copy_reads, !off_dev, j.s, j.lay);
+  j.stage_r = stage_host && L > 0 && !j.reads_dev;
+  j.stage_o = stage_host && !off_dev;
+  j.nf_max = kc::make_shape(shape_opts(p), L, n_reads, k, canonical, j.copy_reads && !j.stage_r,
+                            !off_dev && !j.stage_o, j.s, j.lay);
   j.P1 = 1 << j.s.b1;
   j.ws_bytes = j.lay.total;
   j.out_key_bytes = j.s.cap * j.s.kw * 8;
@@ -322,7 +338,9 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
 kc::Buffers make_buffers(const Job& j, uint8_t* ws) {
   kc::Buffers b = kc::layout_buffers(j.lay, ws);
   if (!j.copy_reads) b.reads = j.reads;
+  if (j.stage_r) b.reads = j.stage_reads;
   if (j.off_dev) b.offsets = j.offsets;
+  if (j.stage_o) b.offsets = j.stage_offs;
   b.out_keys = (uint64_t*)j.okeys;
   b.out_counts = (uint32_t*)j.ocnts;
   return b;
@@ -331,12 +349,12 @@ kc::Buffers make_buffers(const Job& j, uint8_t* ws) {
 // The input copies of one count (reads that are on the host or misaligned, host offsets).
 bool enqueue_copies(const Job& j, const kc::Buffers& b, cudaStream_t st, std::string* err) {
   cudaError_t e;
-  if (j.copy_reads && (e = cudaMemcpyAsync((void*)b.reads, j.reads, j.L,
+  if (j.copy_reads && !j.stage_r && (e = cudaMemcpyAsync((void*)b.reads, j.reads, j.L,
                                            j.reads_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     *err = std::string("copying reads: ") + cudaGetErrorString(e);
     return false;
   }
-  if (!j.off_dev &&
+  if (!j.off_dev && !j.stage_o &&
       (e = cudaMemcpyAsync((void*)b.offsets, j.offsets, (j.n_reads + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     *err = std::string("copying offsets: ") + cudaGetErrorString(e);
     return false;
@@ -417,6 +435,17 @@ struct AsyncJob {
   int slot = -1;
   cudaEvent_t ev = nullptr;
   GroupOwner* owner = nullptr;  // a count of a batched group: its results live in the group's buffers
+  // staged host inputs (allocated for the transfer stream) and the event after their copy
+  void* stage = nullptr;
+  cudaEvent_t ev_in = nullptr;
+  // host buffers the result goes to (kc_job_copy_to_host), the event after that copy, and
+  // the status record kept while it runs
+  uint64_t* keys_host = nullptr;
+  uint32_t* counts_host = nullptr;
+  uint64_t host_cap = 0;
+  cudaEvent_t ev_out = nullptr;
+  bool copying = false;
+  kc::Meta meta{};
 };
 
 // drop one reference to a group's result buffers (freed with the last)
@@ -439,8 +468,20 @@ void retire(kc_plan_s* p, uint64_t id, AsyncJob* a, bool drop) {
     }
   }
   if (a->ev) cudaEventDestroy(a->ev);
+  if (a->ev_in) cudaEventDestroy(a->ev_in);
+  if (a->ev_out) cudaEventDestroy(a->ev_out);
+  dev_free_on(p, a->stage, p->xfer);  // the count that read it has ended (its event was seen)
   if (a->slot >= 0) p->pinned_free.push_back(a->slot);
   p->jobs.erase(id);
+  delete a;
+}
+
+// release a job that failed before its kernels were enqueued: its input copy may be queued
+// on the transfer stream, so that stream is drained before the staging buffer goes back
+void drop_unsubmitted(kc_plan_s* p, AsyncJob* a) {
+  if (a->stage) cudaStreamSynchronize(p->xfer);
+  if (a->ev_in) cudaEventDestroy(a->ev_in);
+  dev_free_on(p, a->stage, p->xfer);
   delete a;
 }
 
@@ -679,6 +720,7 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   if (!p) return fail(KC_EINVAL, "kc_plan_destroy: NULL plan");
   cudaSetDevice(p->device);
   cudaStreamSynchronize(p->stream);
+  if (p->xfer) cudaStreamSynchronize(p->xfer);
   while (!p->jobs.empty()) {  // results never collected
     auto it = p->jobs.begin();
     retire(p, it->first, it->second, true);
@@ -694,6 +736,10 @@ kc_status kc_plan_destroy(kc_plan_t p) {
   dev_free(p, p->btab);
   dev_free(p, p->ws);
   cudaStreamSynchronize(p->stream);
+  if (p->xfer) {
+    cudaStreamSynchronize(p->xfer);
+    cudaStreamDestroy(p->xfer);
+  }
   if (p->profile)
     for (int i = 0; i <= kc_plan_s::kMaxMarks; ++i) cudaEventDestroy(p->ev[i]);
   delete p;
@@ -974,11 +1020,11 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   cudaError_t e = cudaSetDevice(p->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   const bool off_dev = is_device_ptr(offsets);
-  if (!off_dev) {
-    if (offsets[0] != 0 || offsets[n_reads] != n_bases)
-      return fail(KC_EINVAL, "kc_submit: offsets must run from 0 to the base count");
-    for (uint64_t r = 0; r < n_reads; ++r)
-      if (offsets[r + 1] < offsets[r]) return fail(KC_EINVAL, "kc_submit: offsets must be non-decreasing");
+  if (!off_dev && (offsets[0] != 0 || offsets[n_reads] != n_bases))  // their order: checked on the device
+    return fail(KC_EINVAL, "kc_submit: offsets must run from 0 to the base count");
+  if (!p->xfer && (e = cudaStreamCreateWithFlags(&p->xfer, cudaStreamNonBlocking)) != cudaSuccess) {
+    p->xfer = nullptr;
+    return cuda_fail(e, "kc_submit: transfer stream");
   }
   if (!p->pinned) {
     if ((e = cudaMallocHost((void**)&p->pinned, sizeof(kc::Meta) * kc_plan_s::kPinned)) != cudaSuccess)
@@ -987,10 +1033,38 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   }
   if (p->pinned_free.empty()) return fail(KC_EBUSY, "kc_submit: too many counts in flight");
   AsyncJob* a = new AsyncJob();
-  plan_job(p, reads, offsets, n_reads, n_bases, off_dev, k, canonical, a->j);
-  if (p->max_bytes && (uint64_t)(a->j.ws_bytes + a->j.out_key_bytes + a->j.out_cnt_bytes) > p->max_bytes) {
+  plan_job(p, reads, offsets, n_reads, n_bases, off_dev, k, canonical, a->j, true);
+  const size_t stage_r = a->j.stage_r ? (n_bases + 16 + 255) / 256 * 256 : 0;
+  const size_t stage_o = a->j.stage_o ? (n_reads + 1) * 8 : 0;
+  if (p->max_bytes &&
+      (uint64_t)(a->j.ws_bytes + stage_r + stage_o + a->j.out_key_bytes + a->j.out_cnt_bytes) > p->max_bytes) {
     delete a;
     return fail(KC_ENOMEM, "kc_submit: input needs more device memory than max_device_bytes");
+  }
+  // host inputs: copied on the transfer stream into the job's own buffer (allocated for that
+  // stream), the count's kernels wait for the copy's event
+  if (stage_r + stage_o) {
+    a->stage = dev_alloc_on(p, stage_r + stage_o, p->xfer);
+    if (!a->stage) {
+      delete a;
+      return fail(KC_ENOMEM, "kc_submit: input staging allocation failed");
+    }
+    a->j.stage_reads = (const uint8_t*)a->stage;
+    a->j.stage_offs = (const uint64_t*)((uint8_t*)a->stage + stage_r);
+    if ((a->j.stage_r && (e = cudaMemcpyAsync((void*)a->j.stage_reads, reads, n_bases, cudaMemcpyHostToDevice,
+                                              p->xfer)) != cudaSuccess) ||
+        (a->j.stage_o && (e = cudaMemcpyAsync((void*)a->j.stage_offs, offsets, stage_o, cudaMemcpyHostToDevice,
+                                              p->xfer)) != cudaSuccess) ||
+        (e = cudaEventCreateWithFlags(&a->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(a->ev_in, p->xfer)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->stream, a->ev_in, 0)) != cudaSuccess) {
+      cudaStreamSynchronize(p->xfer);
+      cudaStreamSynchronize(p->stream);
+      if (a->ev_in) cudaEventDestroy(a->ev_in);
+      dev_free_on(p, a->stage, p->xfer);
+      delete a;
+      return cuda_fail(e, "kc_submit: copying the inputs");
+    }
   }
   // submitted counts run one after another on the plan's stream (never two at once on the
   // device); the plan's scratch grows in stream order if this count needs more
@@ -1001,7 +1075,7 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
     p->ws_bytes = 0;
     p->ws = dev_alloc(p, a->j.ws_bytes);
     if (!p->ws) {
-      delete a;
+      drop_unsubmitted(p, a);
       return fail(KC_ENOMEM, "kc_submit: scratch allocation failed");
     }
     p->ws_bytes = a->j.ws_bytes;
@@ -1010,7 +1084,7 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   a->j.ocnts = a->j.okeys ? dev_alloc(p, a->j.out_cnt_bytes) : nullptr;
   if (!a->j.okeys || !a->j.ocnts) {
     dev_free(p, a->j.okeys);
-    delete a;
+    drop_unsubmitted(p, a);
     return fail(KC_ENOMEM, "kc_submit: result allocation failed");
   }
   a->slot = p->pinned_free.back();
@@ -1022,6 +1096,7 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   const kc::Marker none;
   if (!enqueue_job(a->j, (uint8_t*)p->ws, lst, &p->pinned[a->slot], none, p->n_sms, &nl, &err)) {
     cudaStreamSynchronize(lst);
+    cudaStreamSynchronize(p->xfer);
     cudaGetLastError();
     retire(p, id, a, true);
     return fail(KC_ECUDA, "kc_submit: " + err);
@@ -1029,6 +1104,7 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   if ((e = cudaEventCreateWithFlags(&a->ev, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventRecord(a->ev, lst)) != cudaSuccess) {
     cudaStreamSynchronize(lst);
+    cudaStreamSynchronize(p->xfer);
     retire(p, id, a, true);
     return cuda_fail(e, "kc_submit: completion event");
   }
@@ -1171,23 +1247,44 @@ static kc_status job_collect(kc_plan_t p, uint64_t id, kc_result* out, int* done
   if (it == p->jobs.end()) return fail(KC_EINVAL, who + ": no such job");
   AsyncJob* a = it->second;
   cudaSetDevice(p->device);
-  const cudaError_t q = block ? cudaEventSynchronize(a->ev) : cudaEventQuery(a->ev);
-  if (q == cudaErrorNotReady) return KC_OK;
-  *done = 1;
-  if (q != cudaSuccess) {
-    retire(p, id, a, true);
-    return cuda_fail(q, who.c_str());
-  }
-  const kc::Meta m = p->pinned[a->slot];
-  std::string msg;
-  const kc_status stc = job_status(a->j, m, who.c_str(), &msg);
-  if (stc != KC_OK) {
+  auto drop = [&](kc_status stc, const std::string& msg) {
+    *done = 1;
+    if (a->stage || a->copying) cudaStreamSynchronize(p->xfer);
     retire(p, id, a, true);
     return fail(stc, msg);
+  };
+  if (!a->copying) {
+    const cudaError_t q = block ? cudaEventSynchronize(a->ev) : cudaEventQuery(a->ev);
+    if (q == cudaErrorNotReady) return KC_OK;
+    if (q != cudaSuccess) return drop(KC_ECUDA, who + ": " + cudaGetErrorString(q));
+    a->meta = p->pinned[a->slot];
+    std::string msg;
+    const kc_status stc = job_status(a->j, a->meta, who.c_str(), &msg);
+    if (stc != KC_OK) return drop(stc, msg);
+    if (a->keys_host) {
+      // the count has ended (its event was seen): its result goes out on the transfer stream,
+      // behind the input copies queued there, while the counts queued after it run
+      const uint64_t n = a->meta.n_distinct;
+      if (n > a->host_cap) return drop(KC_EINVAL, who + ": the result does not fit the host buffers given");
+      cudaError_t e = cudaSuccess;
+      if (n && ((e = cudaMemcpyAsync(a->keys_host, a->j.okeys, n * a->j.s.kw * 8, cudaMemcpyDefault, p->xfer)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpyAsync(a->counts_host, a->j.ocnts, n * 4, cudaMemcpyDefault, p->xfer)) != cudaSuccess))
+        return drop(KC_ECUDA, who + ": copying the result out: " + cudaGetErrorString(e));
+      if ((e = cudaEventRecord(a->ev_out, p->xfer)) != cudaSuccess)
+        return drop(KC_ECUDA, who + ": copy event: " + cudaGetErrorString(e));
+      a->copying = true;
+    }
   }
-  fill_result(a->j, m, out);
+  if (a->copying) {
+    const cudaError_t q = block ? cudaEventSynchronize(a->ev_out) : cudaEventQuery(a->ev_out);
+    if (q == cudaErrorNotReady) return KC_OK;
+    if (q != cudaSuccess) return drop(KC_ECUDA, who + ": copying the result out: " + cudaGetErrorString(q));
+  }
+  *done = 1;
+  fill_result(a->j, a->meta, out);
   out->_owner = a->owner;  // the result keeps the job's reference on the group's buffers
-  record_stats(p, a->j, m);
+  record_stats(p, a->j, a->meta);
   retire(p, id, a, false);
   return KC_OK;
 }
@@ -1199,6 +1296,30 @@ kc_status kc_job_poll(kc_plan_t p, uint64_t job, kc_result* out, int* done) {
 kc_status kc_job_wait(kc_plan_t p, uint64_t job, kc_result* out) {
   int done = 0;
   return job_collect(p, job, out, &done, true);
+}
+
+kc_status kc_job_copy_to_host(kc_plan_t p, uint64_t job, uint64_t* keys_host, uint32_t* counts_host,
+                              uint64_t capacity) {
+  g_err.clear();
+  if (!p || !keys_host || !counts_host) return fail(KC_EINVAL, "kc_job_copy_to_host: NULL argument");
+  ScopedBusy busy(p);
+  if (!busy.ok) return fail(KC_EBUSY, "kc_job_copy_to_host: plan in use by another call");
+  auto it = p->jobs.find(job);
+  if (it == p->jobs.end()) return fail(KC_EINVAL, "kc_job_copy_to_host: no such job");
+  AsyncJob* a = it->second;
+  if (a->copying) return fail(KC_EINVAL, "kc_job_copy_to_host: the job's result is already being copied");
+  cudaSetDevice(p->device);
+  if (!a->ev_out) {
+    const cudaError_t e = cudaEventCreateWithFlags(&a->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      a->ev_out = nullptr;
+      return cuda_fail(e, "kc_job_copy_to_host: copy event");
+    }
+  }
+  a->keys_host = keys_host;
+  a->counts_host = counts_host;
+  a->host_cap = capacity;
+  return KC_OK;
 }
 
 }  // extern "C"

@@ -84,11 +84,16 @@ def test_submit_errors_and_recovery(counter, torch_cuda):
     torch = torch_cuda
     reads = np.frombuffer(b"ACGTACGTAC", dtype=np.uint8).copy()
     bad = np.array([0, 6, 3, 10], dtype=np.uint64)
-    with pytest.raises(KcError) as e:  # host offsets: refused at once, no job
-        counter.submit(reads, bad, 3, True, n_bases=10)
+    with pytest.raises(KcError) as e:  # host offsets whose ends are wrong: refused at once, no job
+        counter.submit(reads, np.array([0, 10], np.uint64), 3, True, n_bases=9)
     assert e.value.status == KC_EINVAL
     with pytest.raises(KcError) as e:
-        counter.submit(reads, np.array([0, 10], np.uint64), 3, True, n_bases=9)
+        counter.submit(reads, np.array([1, 10], np.uint64), 3, True, n_bases=10)
+    assert e.value.status == KC_EINVAL
+    # host offsets out of order: their order is checked on the GPU, reported when collected
+    job = counter.submit(reads, bad, 3, True, n_bases=10)
+    with pytest.raises(KcError) as e:
+        counter.wait(job)
     assert e.value.status == KC_EINVAL
     # device offsets: the GPU finds the error; it is reported when the job is collected
     job = counter.submit(torch.from_numpy(reads).cuda(), torch.from_numpy(bad.astype(np.int64)).cuda(), 3, True,
