@@ -552,7 +552,7 @@ __device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t c1, int k, u128
 template <int KW>
 __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b, uint32_t bid) {
   typedef typename KeyT<KW>::T K;
-  extern __shared__ uint32_t hist_s[];  // [P1]
+  extern __shared__ uint32_t hist_s[];  // [P1 + 1]: the last bin takes the invalid windows
   __shared__ uint64_t code_s[kPackThreads + 2];
   __shared__ uint32_t inv_s[kPackThreads + 2];
   __shared__ uint32_t st_s[kPackThreads + 2];
@@ -560,7 +560,7 @@ __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b
   const int t = threadIdx.x;
   const int P1 = 1 << s.b1;
   const uint64_t tile = bid;
-  for (int c = t; c < P1; c += kPackThreads) hist_s[c] = 0;
+  for (int c = t; c <= P1; c += kPackThreads) hist_s[c] = 0;
   if (t == 0) {
     rcur_s = b.tile_first[tile];
     // bases read: never past the end the offsets give (a base count that disagrees with
@@ -606,9 +606,9 @@ __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b
       const uint32_t vm = valid_mask(inv_s[t], inv_s[t + 1], inv, st_s[t], st_s[t + 1], st_s[t + 2], s.k);
       win_setup<KW, 32>(code_s[t], code_s[t + 1], code, vm, 0, s.k, W);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        if ((W.valid >> i) & 1u)
-          atomicAdd(&hist_s[coarse_field(umap(win_top32<KW, 32>(W, i, s.canonical), s.canonical), s.b1)], 1u);
+      for (int i = 0; i < 32; ++i) {  // an invalid window goes to bin P1, which is never read: no branch
+        const uint32_t c = coarse_field(umap(win_top32<KW, 32>(W, i, s.canonical), s.canonical), s.b1);
+        atomicAdd(&hist_s[((W.valid >> i) & 1u) ? c : (uint32_t)P1], 1u);
       }
     }
   }
@@ -860,8 +860,9 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
       const uint32_t vm = valid_mask(inv_s[sw - 2], inv_s[sw - 1], inv_s[sw], st_s[sw - 2], st_s[sw - 1], st_s[sw], s.k);
       win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], vm, h, s.k, W);
       valid = W.valid & (WPT == 32 ? 0xffffffffu : 0xffffu);
-      // the arithmetic of every window is branch-free (so that the windows' dependency chains
-      // interleave); only the shared-memory updates depend on the window being valid
+      // every window is computed and ranked without a branch (so that the windows' dependency
+      // chains interleave): an invalid window is ranked in bin P1, which no scan reads, and
+      // only the rare sketch update depends on the window being valid
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
         uint64_t c0, c1;
@@ -870,15 +871,16 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
         const uint32_t c = coarse_field(umap((uint32_t)(c0 >> 32), s.canonical), s.b1);
         const uint64_t hh = key_hash(keys[i]);
         const bool v = (valid >> i) & 1u;
-        if (v) {
-          if constexpr (DIRECT) {
+        if constexpr (DIRECT) {
+          if (v) {
             const unsigned long long pos = atomicAdd(&b.fcur[c], 1ull);
             if (pos < s.cap) store_key(b.kbuf, pos, keys[i]);
             else atomicOr(&b.meta->status, ST_INTERNAL);
-          } else {
-            if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
-            rr[i >> 1] |= atomicAdd(&hist[PAD(c)], 1u) << (16 * (i & 1));
           }
+        } else {
+          if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
+          const uint32_t cc = v ? c : (uint32_t)P1;  // bin P1 (never scanned) takes the invalid windows
+          rr[i >> 1] |= (atomicAdd(&hist[PAD(cc)], 1u) & 0xffffu) << (16 * (i & 1));
         }
         if (v && (hh >> (64 - kHllSampleLog2)) == 0) {
           const uint32_t reg = (uint32_t)(hh >> (64 - kHllSampleLog2 - kHllLog2)) & (kHllRegs - 1);
@@ -894,14 +896,15 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
     block_exclusive_scan_pad<uint32_t>(soff, P1, wt);
 #pragma unroll
     for (int i = 0; i < WPT; ++i) {
-      if (valid & (1u << i)) {
-        uint32_t c;
-        if constexpr (KEEP_C) c = rawc[i * NT + t];
-        else c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
-        const uint32_t pos = soff[PAD(c)] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu);
-        stage[pos] = keys[i];
-        if constexpr (KEEP_C) stage_c[pos] = (uint16_t)c;
-      }
+      // an invalid window is staged at slot SUB - 1, which no valid window takes then (with
+      // one window invalid, at most SUB - 1 are valid) and the write-out never reads
+      uint32_t c;
+      if constexpr (KEEP_C) c = rawc[i * NT + t];
+      else c = coarse_of(keys[i], s.k, s.canonical, s.b1);  // same field as above, from the key
+      const uint32_t pos = (valid & (1u << i)) ? soff[PAD(c)] + ((rr[i >> 1] >> (16 * (i & 1))) & 0xffffu)
+                                               : (uint32_t)(SUB - 1);
+      stage[pos] = keys[i];
+      if constexpr (KEEP_C) stage_c[pos] = (uint16_t)c;
     }
     __syncthreads();
     const uint32_t n_sub = soff[PAD(P1 - 1)] + hist[PAD(P1 - 1)];
@@ -2279,7 +2282,7 @@ int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, con
   k_tile_first<<<(unsigned)((s.n_tiles + 127) / 128), 128, 0, st>>>(b.offsets, s.n_reads, s.n_tiles, b.tile_first);
   ++launches;
   KC_STEP("k_tile_first");
-  const size_t smA = (size_t)P1 * 4;
+  const size_t smA = (size_t)(P1 + 1) * 4;
   if (s.kw == 1) k_pack_count<1><<<(unsigned)s.n_tiles, kPackThreads, smA, st>>>(s, b);
   else k_pack_count<2><<<(unsigned)s.n_tiles, kPackThreads, smA, st>>>(s, b);
   ++launches;
@@ -2401,10 +2404,10 @@ int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mar
   KC_BLAUNCH(BK_TILE_FIRST, (k_tile_first_batch<<<bp.grid[BK_TILE_FIRST], 128, 0, st>>>(tab(BK_TILE_FIRST))),
              "k_tile_first");
   if (bp.kw == 1) {
-    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<1><<<bp.grid[BK_PACK], kPackThreads, (size_t)P1 * 4, st>>>(tab(BK_PACK))),
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<1><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 1) * 4, st>>>(tab(BK_PACK))),
                "k_pack_count");
   } else {
-    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<2><<<bp.grid[BK_PACK], kPackThreads, (size_t)P1 * 4, st>>>(tab(BK_PACK))),
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<2><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 1) * 4, st>>>(tab(BK_PACK))),
                "k_pack_count");
   }
   KC_BLAUNCH(BK_COL_SCAN, (k_col_scan_batch<<<bp.grid[BK_COL_SCAN], dim3(32, 32), 0, st>>>(tab(BK_COL_SCAN))),
