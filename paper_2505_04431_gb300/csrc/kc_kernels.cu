@@ -1418,14 +1418,13 @@ __device__ __forceinline__ int count_insert(Table<KW> tb, typename KeyT<KW>::T k
   for (int probe = 0; probe < kProbeLimit; ++probe, s = (s + 1) & mask) {
     int res = 0;
     if constexpr (KW == 1) {
+      // read the slot; claim it only if empty (the claim's answer then replaces the read):
+      // one exit test per probe instead of a branch per case
       uint64_t* p = reinterpret_cast<uint64_t*>(tb.keys) + s;
-      const uint64_t cur = *reinterpret_cast<volatile uint64_t*>(p);
-      if (cur == (uint64_t)key) {
-        res = 1;
-      } else if (cur == ~0ull) {
-        const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(p), ~0ull, (unsigned long long)key);
-        res = old == ~0ull ? 2 : (old == (unsigned long long)key ? 1 : 0);
-      }
+      unsigned long long old = *reinterpret_cast<volatile uint64_t*>(p);
+      const bool emp = old == ~0ull;
+      if (emp) old = atomicCAS(reinterpret_cast<unsigned long long*>(p), ~0ull, (unsigned long long)key);
+      res = (emp && old == ~0ull) ? 2 : (old == (unsigned long long)key ? 1 : 0);
     } else {
       const K old = cas128_shared(reinterpret_cast<u128*>(tb.keys) + s, (u128)EMPTY, (u128)key);
       res = old == EMPTY ? 2 : (old == key ? 1 : 0);
