@@ -38,8 +38,9 @@ constexpr int kFineChunk2 = 4096;              // fine-scatter chunk, 128-bit ke
 constexpr int kFineLocalCap = 2048;            // fine partitions one chunk may span (shared histogram)
 constexpr int kHllLog2 = 10;                   // distinct-key sketch: 1024 registers
 constexpr int kHllRegs = 1 << kHllLog2;
-constexpr int kHllSampleLog2 = 3;              // ... over a 1/8 hash sample of the keys
-constexpr double kHllSample = 8.0;
+constexpr int kHllSampleLog2 = 6;              // ... over a 1/64 hash sample of the keys (a rarer sample
+                                               // leaves pass B's warps out of the sketch update more often)
+constexpr double kHllSample = 64.0;
 constexpr uint32_t kLookbackSpinLimit = 1u << 22;  // x ~100 ns sleep: ~0.4 s, then give up
 constexpr uint32_t kTestSpinLimit = 64;            // the same wait when a test withholds a prefix
 constexpr uint32_t kTestCountLimit = 0xffff;       // the count limit when a test lowers it

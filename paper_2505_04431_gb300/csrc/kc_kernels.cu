@@ -700,7 +700,7 @@ __device__ __forceinline__ void fine_plan_body(const uint64_t* cstart, const uin
   __shared__ float zsum_s[32], zeros_s[32];
   __shared__ double target_s;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // HyperLogLog estimate over the 1/8 hash-sample of the keys
+  // HyperLogLog estimate over the 1/64 hash-sample of the keys
   float z = 0.f, zeros = 0.f;
   for (int i = threadIdx.x; i < kHllRegs; i += blockDim.x) {
     const uint32_t r = hll[i];
@@ -780,7 +780,7 @@ __global__ void k_fine_plan_batch(BatchTab t) {
 // Per sub-step, NT threads x WPT windows: every key is computed once and kept in registers,
 // its rank inside its partition taken with a shared-memory atomic (counting sort, step 1);
 // after the block scan of the partition histogram the keys go to their partition's run in
-// the staging buffer, and the runs leave in order.  A 1/8 hash sample of the keys feeds a
+// the staging buffer, and the runs leave in order.  A 1/64 hash sample of the keys feeds a
 // HyperLogLog sketch (distinct-key estimate for sizing the fine partitions).
 __device__ __forceinline__ uint64_t key_hash(uint64_t key) { return key * 0x9E3779B97F4A7C15ull; }
 __device__ __forceinline__ uint64_t key_hash(u128 key) {
