@@ -339,21 +339,38 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             raise RuntimeError(f"pipelined counts returned {got} entries, expected {D * e2e_steps}")
         keys_h, cnt_h = outs[0]
 
+        # each serial step timed in its own parts as it runs: the count call (its input copy
+        # included) and the result copy, device time by events on the plan's stream and host
+        # wall clock around each call
+        steps_parts = []
+
         def serial_step():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            t_a = time.perf_counter()
+            ev[0].record(stream)
             res = counter.count(r_pin, o_pin, k, True)
+            ev[1].record(stream)
+            t_b = time.perf_counter()
             _check(lib, lib.kc_result_copy_to_host(counter._plan, ctypes.byref(res._res), keys_h.data_ptr(),
                                                    cnt_h.data_ptr()))
+            ev[2].record(stream)
+            t_c = time.perf_counter()
             res.free()
+            steps_parts.append((ev, (t_b - t_a) * 1e3, (t_c - t_b) * 1e3))
 
         serial_step()
         torch.cuda.synchronize()
+        steps_parts.clear()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             serial_step()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
-        # the serial step's parts, host wall clock around each with the stream drained: the
-        # inputs in (the same pinned buffers), the count on those device inputs, the result out
+        sp = np.array([(ev[0].elapsed_time(ev[1]), wa, ev[1].elapsed_time(ev[2]), wb) for ev, wa, wb in steps_parts])
+        in_step = {"count_call_device_ms": float(np.median(sp[:, 0])), "count_call_wall_ms": float(np.median(sp[:, 1])),
+                   "copy_out_device_ms": float(np.median(sp[:, 2])), "copy_out_wall_ms": float(np.median(sp[:, 3]))}
+        # the serial step's parts apart, host wall clock around each with the stream drained:
+        # the inputs in (the same pinned buffers), the count on those device inputs, the result out
         rd = torch.empty_like(r_pin, device=dev)
         od = torch.empty_like(o_pin, device=dev)
         reps = []
@@ -385,7 +402,7 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
                        "(result to pinned host buffers) + kc_job_wait, two counts in flight",
                "serial": {"value": whole_job_rate(K, world, e2e_steps, dt * 1e3), "ms_per_step": dt * 1e3 / e2e_steps,
                           "form": "kc_count (pinned host reads) + kc_result_copy_to_host, one step at a time",
-                          "parts": parts,
+                          "parts": parts, "in_step": in_step,
                           "link_gbs": {"h2d": h2d_bytes / parts["h2d_ms"] / 1e6,
                                        "d2h": d2h_bytes / max(parts["d2h_ms"], 1e-9) / 1e6}}}
 
