@@ -552,7 +552,7 @@ __device__ __forceinline__ void top_to_key(uint64_t c0, uint64_t c1, int k, u128
 template <int KW>
 __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b, uint32_t bid) {
   typedef typename KeyT<KW>::T K;
-  extern __shared__ uint32_t hist_s[];  // [P1 + 1]: the last bin takes the invalid windows
+  extern __shared__ uint32_t hist_s[];  // [P1 + 32]: bins P1 + lane take the invalid windows
   __shared__ uint64_t code_s[kPackThreads + 2];
   __shared__ uint32_t inv_s[kPackThreads + 2];
   __shared__ uint32_t st_s[kPackThreads + 2];
@@ -560,7 +560,7 @@ __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b
   const int t = threadIdx.x;
   const int P1 = 1 << s.b1;
   const uint64_t tile = bid;
-  for (int c = t; c <= P1; c += kPackThreads) hist_s[c] = 0;
+  for (int c = t; c < P1 + 32; c += kPackThreads) hist_s[c] = 0;
   if (t == 0) {
     rcur_s = b.tile_first[tile];
     // bases read: never past the end the offsets give (a base count that disagrees with
@@ -606,9 +606,9 @@ __device__ __forceinline__ void pack_count_body(const Shape& s, const Buffers& b
       const uint32_t vm = valid_mask(inv_s[t], inv_s[t + 1], inv, st_s[t], st_s[t + 1], st_s[t + 2], s.k);
       win_setup<KW, 32>(code_s[t], code_s[t + 1], code, vm, 0, s.k, W);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {  // an invalid window goes to bin P1, which is never read: no branch
+      for (int i = 0; i < 32; ++i) {  // an invalid window goes to bin P1 + lane, never read: no branch
         const uint32_t c = coarse_field(umap(win_top32<KW, 32>(W, i, s.canonical), s.canonical), s.b1);
-        atomicAdd(&hist_s[((W.valid >> i) & 1u) ? c : (uint32_t)P1], 1u);
+        atomicAdd(&hist_s[((W.valid >> i) & 1u) ? c : (uint32_t)P1 + (t & 31)], 1u);
       }
     }
   }
@@ -804,8 +804,8 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
   K* stage = reinterpret_cast<K*>(sm);                                                // [SUB]
   unsigned long long* cursor = reinterpret_cast<unsigned long long*>(stage + SUB);   // [P1] absolute write positions
   uint32_t* hist = reinterpret_cast<uint32_t*>(cursor + P1);                            // [padded P1]
-  uint32_t* soff = hist + padded_len(P1);                                               // [padded P1]
-  uint16_t* rawc = reinterpret_cast<uint16_t*>(soff + padded_len(P1));  // KEEP_C: [SUB], window i of thread t at i * NT + t
+  uint32_t* soff = hist + padded_len(P1 + 32);                                          // [padded P1]
+  uint16_t* rawc = reinterpret_cast<uint16_t*>(soff + padded_len(P1 + 32));  // KEEP_C: [SUB], window i of thread t at i * NT + t
   uint16_t* stage_c = rawc + SUB;                                        // KEEP_C: [SUB], partition of each staged key
   __shared__ uint64_t code_s[NW + 2];
   __shared__ uint32_t inv_s[NW + 2];
@@ -861,7 +861,8 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
       win_setup<KW, WPT>(code_s[sw - 2], code_s[sw - 1], code_s[sw], vm, h, s.k, W);
       valid = W.valid & (WPT == 32 ? 0xffffffffu : 0xffffu);
       // every window is computed and ranked without a branch (so that the windows' dependency
-      // chains interleave): an invalid window is ranked in bin P1, which no scan reads, and
+      // chains interleave): an invalid window is ranked in bin P1 + lane, which no scan reads
+      // (one such bin per lane, so that a warp's invalid windows do not share an address), and
       // only the rare sketch update depends on the window being valid
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
@@ -879,7 +880,7 @@ __device__ __forceinline__ void scatter_body(const Shape& s, const Buffers& b, u
           }
         } else {
           if constexpr (KEEP_C) rawc[i * NT + t] = (uint16_t)c;
-          const uint32_t cc = v ? c : (uint32_t)P1;  // bin P1 (never scanned) takes the invalid windows
+          const uint32_t cc = v ? c : (uint32_t)P1 + (t & 31);
           rr[i >> 1] |= (atomicAdd(&hist[PAD(cc)], 1u) & 0xffffu) << (16 * (i & 1));
         }
         if (v && (hh >> (64 - kHllSampleLog2)) == 0) {
@@ -2201,7 +2202,7 @@ __global__ void __launch_bounds__(256) k_compact_batch(BatchTab t) {
 constexpr size_t kScatterStaticSmem = 9216;  // pass B's static shared memory (batched form included), rounded up
 static size_t scatter_smem(int kw, int nt, int P1, bool keep_c) {
   const size_t sub = (size_t)nt * (kw == 1 ? 32 : 16);
-  return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1) * 4 + (keep_c ? sub * 4 : 0);
+  return sub * (size_t)(kw * 8) + (size_t)P1 * 8 + 2 * padded_len(P1 + 32) * 4 + (keep_c ? sub * 4 : 0);
 }
 static size_t fine_hist_smem(int P1) { return (size_t)(P1 + 1) * 8 + kFineLocalCap * 4 + 16; }
 static size_t fine_scatter_smem(int kw, int P1) {
@@ -2281,7 +2282,7 @@ int launch_phase1(const Shape& s, const Buffers& b, int n_sms, void* stream, con
   k_tile_first<<<(unsigned)((s.n_tiles + 127) / 128), 128, 0, st>>>(b.offsets, s.n_reads, s.n_tiles, b.tile_first);
   ++launches;
   KC_STEP("k_tile_first");
-  const size_t smA = (size_t)(P1 + 1) * 4;
+  const size_t smA = (size_t)(P1 + 32) * 4;
   if (s.kw == 1) k_pack_count<1><<<(unsigned)s.n_tiles, kPackThreads, smA, st>>>(s, b);
   else k_pack_count<2><<<(unsigned)s.n_tiles, kPackThreads, smA, st>>>(s, b);
   ++launches;
@@ -2403,10 +2404,10 @@ int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mar
   KC_BLAUNCH(BK_TILE_FIRST, (k_tile_first_batch<<<bp.grid[BK_TILE_FIRST], 128, 0, st>>>(tab(BK_TILE_FIRST))),
              "k_tile_first");
   if (bp.kw == 1) {
-    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<1><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 1) * 4, st>>>(tab(BK_PACK))),
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<1><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 32) * 4, st>>>(tab(BK_PACK))),
                "k_pack_count");
   } else {
-    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<2><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 1) * 4, st>>>(tab(BK_PACK))),
+    KC_BLAUNCH(BK_PACK, (k_pack_count_batch<2><<<bp.grid[BK_PACK], kPackThreads, (size_t)(P1 + 32) * 4, st>>>(tab(BK_PACK))),
                "k_pack_count");
   }
   KC_BLAUNCH(BK_COL_SCAN, (k_col_scan_batch<<<bp.grid[BK_COL_SCAN], dim3(32, 32), 0, st>>>(tab(BK_COL_SCAN))),
