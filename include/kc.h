@@ -93,6 +93,11 @@ typedef struct {
 /* Testing: counts above 2^16 - 1 are reported as overflowing (KC_EOVERFLOW), so that the
  * overflow report can be checked without an input of 2^32 windows of one k-mer. */
 #define KC_PLAN_TEST_COUNT_LIMIT 64u
+/* Testing: fine partition regions sized from a sample of the keys at any input size (by
+ * default only counts of at least 2^26 bases do), and, with the second flag, without slack,
+ * so that regions overflow and the exact fine split that follows is exercised. */
+#define KC_PLAN_TEST_FINE_SAMPLED 128u
+#define KC_PLAN_TEST_TIGHT_SLACK 256u
 
 typedef struct {
   uint64_t n;               /* number of distinct keys */
@@ -166,6 +171,10 @@ typedef struct {
   uint64_t sub_cycles[8];      /* KC_PLAN_PROFILE only: cycles of the ordering sub-steps (key
                                   range, rank, scan, place, small sorts, large sorts) and the
                                   number of large buckets */
+  uint32_t fine_sampled;       /* 1 if the fine partitions' regions were sized from a sample
+                                  of the keys (large single counts) */
+  uint32_t fine_resplit;       /* 1 if a sampled region overflowed and the exact fine split
+                                  ran instead (the result is the same either way) */
 } kc_stats;
 kc_status kc_last_stats(kc_plan_t plan, kc_stats *out);
 

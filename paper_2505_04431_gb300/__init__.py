@@ -38,6 +38,8 @@ KC_PLAN_ABLATE_NO_SMEM_BUCKETS = 8
 KC_PLAN_WARP_MERGE = 16
 KC_PLAN_TEST_WITHHOLD_PREFIX = 32
 KC_PLAN_TEST_COUNT_LIMIT = 64
+KC_PLAN_TEST_FINE_SAMPLED = 128
+KC_PLAN_TEST_TIGHT_SLACK = 256
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -61,7 +63,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint32), ("n_partitions", ctypes.c_uint32),
                 ("n_fine", ctypes.c_uint64), ("n_overflow_fine", ctypes.c_uint64), ("n_deferred_fine", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("phase_cycles", ctypes.c_uint64 * 8),
-                ("sub_cycles", ctypes.c_uint64 * 8)]
+                ("sub_cycles", ctypes.c_uint64 * 8), ("fine_sampled", ctypes.c_uint32),
+                ("fine_resplit", ctypes.c_uint32)]
 
 
 class KcError(RuntimeError):
@@ -206,7 +209,8 @@ class KmerCounter:
                  n_partitions_hint: int = 0, table_load: float = 0.0, table_slots_max: int = 0,
                  max_device_bytes: int = 0, profile: bool = False, defer_all: bool = False,
                  small_batch_arena: bool = False, no_smem_buckets: bool = False, warp_merge: bool = False,
-                 test_withhold_prefix: bool = False, test_count_limit: bool = False):
+                 test_withhold_prefix: bool = False, test_count_limit: bool = False,
+                 test_fine_sampled: bool = False, test_tight_slack: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("KmerCounter needs a CUDA device (no CPU fallback)")
@@ -248,7 +252,9 @@ class KmerCounter:
                       | (KC_PLAN_ABLATE_NO_SMEM_BUCKETS if no_smem_buckets else 0)
                       | (KC_PLAN_WARP_MERGE if warp_merge else 0)
                       | (KC_PLAN_TEST_WITHHOLD_PREFIX if test_withhold_prefix else 0)
-                      | (KC_PLAN_TEST_COUNT_LIMIT if test_count_limit else 0))
+                      | (KC_PLAN_TEST_COUNT_LIMIT if test_count_limit else 0)
+                      | (KC_PLAN_TEST_FINE_SAMPLED if test_fine_sampled else 0)
+                      | (KC_PLAN_TEST_TIGHT_SLACK if test_tight_slack else 0))
         plan = ctypes.c_void_p()
         _check(lib, lib.kc_plan(ctypes.byref(opts), ctypes.byref(plan)))
         self._opts = opts

@@ -87,6 +87,11 @@ uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int
   const uint64_t nf_bound = s.cap / s.fine_target + P1 + 1;
   const uint64_t nf_lim = P1 * kMaxFine;
   s.nf_max = nf_bound < nf_lim ? nf_bound : nf_lim;
+  // a sampled fine layout: regions hold their estimate plus slack (about a fifth of the keys
+  // in all, and at least 16 keys each); a layout that does not fit falls back to the exact one
+  s.fine_sampled = o.allow_sampled && (o.force_sampled || L >= kFineSampledMinBases) ? 1 : 0;
+  s.tight_slack = o.tight_slack;
+  s.cap_kb = s.fine_sampled ? s.cap + s.cap / 4 + s.nf_max * 64 : s.cap;
   s.smem_budget = o.smem_optin;
   s.spin_limit = o.withhold ? kTestSpinLimit : kLookbackSpinLimit;
   s.count_limit = o.low_count_limit ? kTestCountLimit : 0xffffffffu;
@@ -117,8 +122,8 @@ uint32_t make_shape(const ShapeOpts& o, uint64_t L, uint64_t n_reads, int k, int
   lay.flo = take((nf + 1) * 4);
   lay.fc = take(nf * 8);
   lay.look = take(nf * 8);
-  lay.kbuf = take(s.cap * s.kw * 8);
-  lay.sbuf = take(s.cap * s.kw * 8);
+  lay.kbuf = take(s.cap_kb * s.kw * 8);
+  lay.sbuf = take(s.cap_kb * s.kw * 8);
   lay.meta = take(sizeof(Meta));
   lay.total = at;
   return (uint32_t)nf;
@@ -208,6 +213,8 @@ struct kc_plan_s {
   bool defer_all = false;
   bool withhold = false;
   bool low_count_limit = false;
+  bool force_sampled = false;
+  bool tight_slack = false;
   bool small_arena = false;
   int aggr = 0;
   static constexpr int kMaxMarks = 32;
@@ -311,12 +318,14 @@ kc::ShapeOpts shape_opts(const kc_plan_s* p) {
   o.defer_all = p->defer_all ? 1 : 0;
   o.withhold = p->withhold ? 1 : 0;
   o.low_count_limit = p->low_count_limit ? 1 : 0;
+  o.force_sampled = p->force_sampled ? 1 : 0;
+  o.tight_slack = p->tight_slack ? 1 : 0;
   o.aggr = p->aggr;
   return o;
 }
 
 void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t L,
-              bool off_dev, int k, int canonical, Job& j, bool stage_host = false) {
+              bool off_dev, int k, int canonical, Job& j, bool stage_host = false, bool single = false) {
   j.reads = reads;
   j.offsets = offsets;
   j.n_reads = n_reads;
@@ -326,8 +335,10 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   j.copy_reads = L > 0 && (!j.reads_dev || ((uintptr_t)reads & 15) != 0);
   j.stage_r = stage_host && L > 0 && !j.reads_dev;
   j.stage_o = stage_host && !off_dev;
-  j.nf_max = kc::make_shape(shape_opts(p), L, n_reads, k, canonical, j.copy_reads && !j.stage_r,
-                            !off_dev && !j.stage_o, j.s, j.lay);
+  kc::ShapeOpts o = shape_opts(p);
+  o.allow_sampled = single ? 1 : 0;  // batched counts keep the exact fine layout
+  j.nf_max = kc::make_shape(o, L, n_reads, k, canonical, j.copy_reads && !j.stage_r, !off_dev && !j.stage_o, j.s,
+                            j.lay);
   j.P1 = 1 << j.s.b1;
   j.ws_bytes = j.lay.total;
   j.out_key_bytes = j.s.cap * j.s.kw * 8;
@@ -650,6 +661,8 @@ void record_stats(kc_plan_s* p, const Job& j, const kc::Meta& m) {
   p->stats.n_fine = m.n_fine;
   p->stats.n_overflow_fine = m.n_overflow;
   p->stats.n_deferred_fine = m.n_deferred;
+  p->stats.fine_sampled = j.s.fine_sampled ? 1u : 0u;
+  p->stats.fine_resplit = m.fine_spill ? 1u : 0u;
   for (int i = 0; i < 8; ++i) p->stats.phase_cycles[i] = m.phase_cycles[i];
   for (int i = 0; i < 8; ++i) p->stats.sub_cycles[i] = m.sub_cycles[i];
 }
@@ -699,6 +712,8 @@ kc_status kc_plan(const kc_plan_opts* opts, kc_plan_t* out) {
   p->defer_all = (opts->flags & KC_PLAN_DEFER_ALL) != 0;
   p->withhold = (opts->flags & KC_PLAN_TEST_WITHHOLD_PREFIX) != 0;
   p->low_count_limit = (opts->flags & KC_PLAN_TEST_COUNT_LIMIT) != 0;
+  p->force_sampled = (opts->flags & KC_PLAN_TEST_FINE_SAMPLED) != 0;
+  p->tight_slack = (opts->flags & KC_PLAN_TEST_TIGHT_SLACK) != 0;
   p->small_arena = (opts->flags & KC_PLAN_BATCH_ARENA_SMALL) != 0;
   p->aggr = ((opts->flags & KC_PLAN_ABLATE_NO_SMEM_BUCKETS) ? kc::kAggrNoSmemBuckets : 0) |
             ((opts->flags & KC_PLAN_WARP_MERGE) ? kc::kAggrWarpMerge : 0);
@@ -753,7 +768,9 @@ kc_status kc_footprint(kc_plan_t p, uint64_t n_reads, uint64_t n_bases, int k, i
   if (k < 1 || k > 64) return fail(KC_EINVAL, "kc_footprint: k must be in 1..64");
   kc::Shape s{};
   kc::Layout lay{};
-  kc::make_shape(shape_opts(p), n_bases, n_reads, k, 1, n_bases > 0 && !reads_on_device, !offsets_on_device, s, lay);
+  kc::ShapeOpts o = shape_opts(p);
+  o.allow_sampled = 1;  // as kc_count and kc_submit size a count
+  kc::make_shape(o, n_bases, n_reads, k, 1, n_bases > 0 && !reads_on_device, !offsets_on_device, s, lay);
   *scratch_bytes = lay.total;
   *result_bytes = s.cap * s.kw * 8 + s.cap * 4;
   return KC_OK;
@@ -835,7 +852,7 @@ kc_status kc_count(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, u
   if (L > 0 && !reads) return fail(KC_EINVAL, "kc_count: reads must not be NULL");
 
   Job j;
-  plan_job(p, reads, offsets, n_reads, L, off_dev, k, canonical, j);
+  plan_job(p, reads, offsets, n_reads, L, off_dev, k, canonical, j, false, true);
   if (p->max_bytes && (uint64_t)(j.ws_bytes + j.out_key_bytes + j.out_cnt_bytes) > p->max_bytes)
     return fail(KC_ENOMEM, "kc_count: input needs more device memory than max_device_bytes");
   if (p->ws_bytes < j.ws_bytes) {
@@ -1033,7 +1050,7 @@ kc_status kc_submit(kc_plan_t p, const uint8_t* reads, const uint64_t* offsets, 
   }
   if (p->pinned_free.empty()) return fail(KC_EBUSY, "kc_submit: too many counts in flight");
   AsyncJob* a = new AsyncJob();
-  plan_job(p, reads, offsets, n_reads, n_bases, off_dev, k, canonical, a->j, true);
+  plan_job(p, reads, offsets, n_reads, n_bases, off_dev, k, canonical, a->j, true, true);
   const size_t stage_r = a->j.stage_r ? (n_bases + 16 + 255) / 256 * 256 : 0;
   const size_t stage_o = a->j.stage_o ? (n_reads + 1) * 8 : 0;
   if (p->max_bytes &&

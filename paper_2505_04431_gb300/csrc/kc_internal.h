@@ -44,6 +44,11 @@ constexpr double kHllSample = 64.0;
 constexpr uint32_t kLookbackSpinLimit = 1u << 22;  // x ~100 ns sleep: ~0.4 s, then give up
 constexpr uint32_t kTestSpinLimit = 64;            // the same wait when a test withholds a prefix
 constexpr uint32_t kTestCountLimit = 0xffff;       // the count limit when a test lowers it
+// Fine layout from a sample: the fine histogram counts one 4096-key chunk in 2^kFineSampleLog2
+// and sizes each fine partition's region from that estimate plus slack; for counts of at
+// least kFineSampledMinBases bases (smaller ones take the exact histogram).
+constexpr int kFineSampleLog2 = 3;
+constexpr uint64_t kFineSampledMinBases = 1ull << 26;
 
 // status bits written by kernels (a kc_status is derived from them on the host)
 enum : uint32_t {
@@ -62,7 +67,7 @@ struct Meta {
   uint64_t n_overflow;  // fine partitions that took the overflow path
   uint64_t n_deferred;  // fine partitions written out by k_compact (prefix unknown in time)
   uint32_t status;
-  uint32_t pad;
+  uint32_t fine_spill;  // the sampled fine layout overflowed a region: the exact fine split ran
   uint64_t ticket;      // phase-2 work counter
   uint64_t d_estimate;  // distinct keys estimated by the sketch
   uint64_t sub_cycles[8];    // profiled plans only: ordering sub-steps (range, rank, scan, place, small sorts, big sorts, #big)
@@ -86,6 +91,9 @@ struct Shape {
   uint64_t smem_budget; // opt-in shared memory per block
   uint32_t spin_limit;  // iterations of a bounded device wait before it gives up
   uint32_t count_limit; // largest count reported (2^32 - 1; lower only when a test asks)
+  uint64_t cap_kb;      // capacity of kbuf / sbuf in keys (cap, plus the slack of a sampled fine layout)
+  int fine_sampled;     // nonzero: fine partition regions sized from a sample of the keys
+  int tight_slack;      // nonzero (testing): sampled regions get no slack
   int profile;          // nonzero: k_count_emit accumulates per-phase cycle counts
   int defer_all;        // nonzero (testing): every fine partition takes the deferred write-out
   int withhold;         // nonzero (testing): partition 0 never publishes its prefix
@@ -183,6 +191,9 @@ struct ShapeOpts {
   size_t smem_optin = 0;
   size_t smem_per_sm = 0;   // shared memory of one SM (for the count blocks it holds)
   int profile = 0, defer_all = 0, withhold = 0, low_count_limit = 0, aggr = 0;
+  int allow_sampled = 0;   // a single count: the fine layout may be sized from a sample
+  int force_sampled = 0;   // testing: sampled at any size
+  int tight_slack = 0;     // testing: sampled regions get no slack
 };
 struct Layout {  // byte offsets into the count's scratch block
   size_t reads, offs, codes, inv, tf, hist, toff, cst, fb, fm, hll, fh, fo, flo, fc, look, kbuf, sbuf, meta;

@@ -1027,9 +1027,13 @@ __device__ __forceinline__ void fetch_bounds(const uint64_t* kbuf, uint64_t c0, 
 }
 
 template <int KW>
-__device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
+__device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk,
+                                               bool redo = false) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
+  if (redo && !b.meta->fine_spill) return;  // the exact fine split runs again only after a spill
+  // a sampled layout counts one chunk in 2^kFineSampleLog2 (the exact split: every chunk)
+  const uint64_t cstep = (s.fine_sampled && !redo) ? ((uint64_t)kFineChunk << kFineSampleLog2) : (uint64_t)kFineChunk;
   const int P1 = 1 << s.b1;
   uint2* fmap = reinterpret_cast<uint2*>(sm);                    // [P1 + 1]
   uint32_t* lh = reinterpret_cast<uint32_t*>(fmap + P1 + 1);     // [kFineLocalCap]
@@ -1038,14 +1042,14 @@ __device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b,
   for (int i = threadIdx.x; i < kFineLocalCap; i += kFineThreads) lh[i] = 0;
   const FineMap x = make_fine_map(s);
   const uint64_t K_total = min(b.meta->n_windows, s.cap);
-  const uint64_t stride = (uint64_t)nblk * kFineChunk;
-  if (threadIdx.x == 0 && bid * (uint64_t)kFineChunk < K_total) {
-    fetch_bounds<KW>(b.kbuf, bid * (uint64_t)kFineChunk, K_total, bnd_s[0]);
+  const uint64_t stride = (uint64_t)nblk * cstep;
+  if (threadIdx.x == 0 && bid * cstep < K_total) {
+    fetch_bounds<KW>(b.kbuf, bid * cstep, K_total, bnd_s[0]);
     cp_async_wait_all();
   }
   __syncthreads();
   int cur = 0;
-  for (uint64_t c0 = bid * (uint64_t)kFineChunk; c0 < K_total; c0 += stride, cur ^= 1) {
+  for (uint64_t c0 = bid * cstep; c0 < K_total; c0 += stride, cur ^= 1) {
     const uint64_t c1 = min(K_total, c0 + kFineChunk);
     const uint32_t g_lo = fmap[coarse_of(bnd_s[cur][0], s.k, s.canonical, s.b1)].x;
     const uint32_t span = fmap[coarse_of(bnd_s[cur][1], s.k, s.canonical, s.b1) + 1].x - g_lo;
@@ -1079,8 +1083,8 @@ __device__ __forceinline__ void fine_hist_body(const Shape& s, const Buffers& b,
   }
 }
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b) {
-  fine_hist_body<KW>(s, b, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers b, int redo) {
+  fine_hist_body<KW>(s, b, blockIdx.x, gridDim.x, redo != 0);
 }
 template <int KW>
 __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t) {
@@ -1088,10 +1092,37 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t)
   fine_hist_body<KW>(d.s, d.b, bid, nblk);
 }
 
-// Exclusive scan of the fine histogram (one block of 1024 threads).
-__device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b) {
+// Keys at positions below x of the keys array that a sampled fine histogram counts: one
+// kFineChunk-key chunk in 2^kFineSampleLog2.
+__device__ __forceinline__ uint64_t sampled_below(uint64_t x) {
+  const uint64_t per = (uint64_t)kFineChunk << kFineSampleLog2;
+  const uint64_t r = x % per;
+  return (x / per) * kFineChunk + (r < (uint64_t)kFineChunk ? r : (uint64_t)kFineChunk);
+}
+
+// Region of fine partition g in a sampled layout: its estimated size (its sampled count
+// scaled by its coarse partition's keys over that partition's sampled keys) plus 5.5
+// standard deviations of that estimate and 16 keys; never more than its coarse partition.
+// Too small a sample gives the whole coarse partition.
+__device__ __forceinline__ uint64_t fine_region(const Shape& sh, const Buffers& b, uint64_t g) {
+  const uint32_t c = sh.b1 ? b.flo[g] >> (32 - sh.b1) : 0u;
+  const uint64_t a = b.cstart[c], e = b.cstart[c + 1];
+  const uint64_t n_c = e - a, s_c = sampled_below(e) - sampled_below(a);
+  if (s_c < 1024) return n_c;
+  const float f = (float)n_c / (float)s_c, cnt = (float)b.fhist[g];
+  const float slack = sh.tight_slack ? 0.f : 5.5f * f * sqrtf(cnt + 1.f) + 16.f;
+  const uint64_t r = (uint64_t)(cnt * f + slack) + (sh.tight_slack ? 0 : 1);
+  return r < n_c ? r : n_c;
+}
+
+// Exclusive scan of the fine partitions' sizes (exact histogram) or regions (sampled
+// layout) into their starts (one block of 1024 threads).  A sampled layout that does not fit
+// the keys arrays is given up at once (the exact split follows).
+__device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b, bool redo = false) {
   __shared__ uint64_t wt[32];
   __shared__ uint64_t carry_s;
+  if (redo && !b.meta->fine_spill) return;
+  const bool sampled = sh.fine_sampled && !redo;
   const uint64_t NF = min(b.meta->n_fine, sh.nf_max);
   const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
   if (t == 0) carry_s = 0;
@@ -1102,7 +1133,7 @@ __device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const uint64_t i = base + (uint64_t)t * 8 + m;
-      v[m] = i < NF ? b.fhist[i] : 0;
+      v[m] = i < NF ? (sampled ? fine_region(sh, b, i) : (uint64_t)b.fhist[i]) : 0;
       s += v[m];
     }
     uint64_t x = s;
@@ -1137,9 +1168,19 @@ __device__ __forceinline__ void fine_scan_body(const Shape& sh, const Buffers& b
     if (t == 0) carry_s += wt[31];
     __syncthreads();
   }
-  if (t == 0) b.foff[NF] = carry_s;
+  if (t == 0) {
+    b.foff[NF] = carry_s;
+    if (sampled && carry_s > sh.cap_kb) b.meta->fine_spill = 1;
+  }
 }
-__global__ void k_fine_scan(Shape sh, Buffers b) { fine_scan_body(sh, b); }
+__global__ void k_fine_scan(Shape sh, Buffers b, int redo) { fine_scan_body(sh, b, redo != 0); }
+
+// Before the exact fine split runs again (a sampled region overflowed): a fresh histogram.
+__global__ void k_fine_redo_clear(Shape sh, Buffers b) {
+  if (!b.meta->fine_spill) return;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < sh.nf_max; i += (uint64_t)gridDim.x * blockDim.x)
+    b.fhist[i] = 0;
+}
 __global__ void k_fine_scan_batch(BatchTab t) {
   KC_BATCH_PROLOGUE(t);
   fine_scan_body(d.s, d.b);
@@ -1185,9 +1226,16 @@ __device__ uint32_t block_scan_to(const uint32_t* in, uint32_t* out, int n, uint
 // partition's global cursor once per chunk, stage the keys grouped by fine partition and
 // write every group as one contiguous run.
 template <int KW>
-__device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk) {
+__device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers& b, uint32_t bid, uint32_t nblk,
+                                                  bool redo = false) {
   typedef typename KeyT<KW>::T K;
   extern __shared__ __align__(16) uint8_t sm[];
+  // the exact split runs again only after a spill; a sampled layout given up by the scan is
+  // not written at all.  In a sampled layout a run that would pass its region's end is not
+  // written: the spill is recorded and the exact split follows.
+  if (redo ? !b.meta->fine_spill : (s.fine_sampled && b.meta->fine_spill)) return;
+  const bool sampled = s.fine_sampled && !redo;
+  constexpr uint64_t kSpilledRun = 1ull << 63;  // never a run's offset
   const int P1 = 1 << s.b1;
   K* stage = reinterpret_cast<K*>(sm);                                          // [kFineChunk]
   uint16_t* stage_g = reinterpret_cast<uint16_t*>(stage + kFineChunk);          // [kFineChunk]
@@ -1222,7 +1270,8 @@ __device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers&
           load_key(b.kbuf, i, key);
           const uint32_t g = fine_of(key, x, fmap);
           const uint64_t pos = g < s.nf_max ? atomicAdd(&b.fcur[g], 1ull) : ~0ull;
-          if (pos < s.cap) store_key(b.sbuf, pos, key);
+          if (sampled && g < s.nf_max && pos >= b.foff[g + 1]) b.meta->fine_spill = 1;
+          else if (pos < s.cap_kb) store_key(b.sbuf, pos, key);
           else atomicOr(&b.meta->status, ST_INTERNAL);
         }
       }
@@ -1246,10 +1295,17 @@ __device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers&
       for (uint32_t i = threadIdx.x; i < span; i += kFineThreads) {
         const uint32_t v = lh[i];
         if (v) {
-          uint64_t gb = s.cap;  // positions at or past cap are rejected below
-          if (g_lo + i < s.nf_max) gb = atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v);
-          else atomicOr(&b.meta->status, ST_INTERNAL);
-          delta[i] = gb - soff[i];
+          uint64_t gb = s.cap_kb;  // positions at or past cap_kb are rejected below
+          if (g_lo + i < s.nf_max) {
+            gb = atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v);
+            if (sampled && gb + v > b.foff[g_lo + i + 1]) {  // the run passes its region's end
+              b.meta->fine_spill = 1;
+              gb = kSpilledRun;
+            }
+          } else {
+            atomicOr(&b.meta->status, ST_INTERNAL);
+          }
+          delta[i] = gb == kSpilledRun ? kSpilledRun : gb - soff[i];
           lh[i] = 0;
         }
       }
@@ -1264,8 +1320,10 @@ __device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers&
       }
       __syncthreads();
       for (uint32_t i = threadIdx.x; i < n_staged; i += kFineThreads) {
-        const uint64_t pos = delta[stage_g[i]] + i;
-        if (pos < s.cap) store_key(b.sbuf, pos, stage[i]);
+        const uint64_t dl = delta[stage_g[i]];
+        if (dl == kSpilledRun) continue;
+        const uint64_t pos = dl + i;
+        if (pos < s.cap_kb) store_key(b.sbuf, pos, stage[i]);
         else atomicOr(&b.meta->status, ST_INTERNAL);
       }
     }
@@ -1274,8 +1332,8 @@ __device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers&
   }
 }
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b) {
-  fine_scatter_body<KW>(s, b, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffers b, int redo) {
+  fine_scatter_body<KW>(s, b, blockIdx.x, gridDim.x, redo != 0);
 }
 template <int KW>
 __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter_batch(BatchTab t) {
@@ -1817,7 +1875,7 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
     next_s[0] = nx;
     if (nx < NF) {
       cp_async8(&next_s[1], &b.foff[nx]);
-      cp_async8(&next_s[2], &b.foff[nx + 1]);
+      cp_async8(&next_s[2], &b.fcur[nx]);  // the split's cursor: the partition's keys end there
       cp_async4(&next_u[0], &b.flo[nx]);
       cp_async4(&next_u[1], &b.flo[nx + 1]);
     }
@@ -1838,7 +1896,7 @@ __device__ __forceinline__ void count_emit_body(const Shape& s, const Buffers& b
       special_s = 0;
       nnew_s = 0;
     }
-    if (f0 > s.cap || n > s.cap - f0) {  // inconsistent scan: record it, count nothing
+    if (f0 > s.cap_kb || n > s.cap_kb - f0) {  // inconsistent scan: record it, count nothing
       if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
       n = 0;
     }
@@ -2176,7 +2234,7 @@ __device__ __forceinline__ void compact_body(const Shape& s, const Buffers& b, u
     }
     const uint32_t d = b.fhist[g] & 0x7fffffffu;
     const uint64_t src = b.foff[g], dst = b.fcur[g];
-    if (src + d > s.cap || dst + d > s.cap) {
+    if (src + d > s.cap_kb || dst + d > s.cap) {
       if (threadIdx.x == 0) atomicOr(&b.meta->status, ST_INTERNAL);
       continue;
     }
@@ -2332,17 +2390,26 @@ int launch_phase2(const Shape& s, const Buffers& b, int n_sms, uint32_t nf_max, 
   ++launches;
   KC_STEP("k_fine_plan");
   const unsigned gf = (unsigned)(n_sms * 2);
-  if (s.kw == 1) k_fine_hist<1><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);
-  else k_fine_hist<2><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b);
-  ++launches;
-  KC_STEP("k_fine_hist");
-  k_fine_scan<<<1, 1024, 0, st>>>(s, b);
-  ++launches;
-  KC_STEP("k_fine_scan");
-  if (s.kw == 1) k_fine_scatter<1><<<gf, kFineThreads, fine_scatter_smem(1, P1), st>>>(s, b);
-  else k_fine_scatter<2><<<gf, kFineThreads, fine_scatter_smem(2, P1), st>>>(s, b);
-  ++launches;
-  KC_STEP("k_fine_scatter");
+  // the fine split (sampled layout or exact); after a sampled one, the exact split again,
+  // whose kernels return at once unless a sampled region overflowed
+  for (int redo = 0; redo <= (s.fine_sampled ? 1 : 0); ++redo) {
+    if (redo) {
+      k_fine_redo_clear<<<(unsigned)n_sms, 1024, 0, st>>>(s, b);
+      ++launches;
+      KC_STEP("k_fine_redo_clear");
+    }
+    if (s.kw == 1) k_fine_hist<1><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b, redo);
+    else k_fine_hist<2><<<gf, kFineThreads, fine_hist_smem(P1), st>>>(s, b, redo);
+    ++launches;
+    KC_STEP(redo ? "k_fine_hist_redo" : "k_fine_hist");
+    k_fine_scan<<<1, 1024, 0, st>>>(s, b, redo);
+    ++launches;
+    KC_STEP(redo ? "k_fine_scan_redo" : "k_fine_scan");
+    if (s.kw == 1) k_fine_scatter<1><<<gf, kFineThreads, fine_scatter_smem(1, P1), st>>>(s, b, redo);
+    else k_fine_scatter<2><<<gf, kFineThreads, fine_scatter_smem(2, P1), st>>>(s, b, redo);
+    ++launches;
+    KC_STEP(redo ? "k_fine_scatter_redo" : "k_fine_scatter");
+  }
   const size_t smC = count_kernel_smem(s.kw, s.bT_max, s.tail);
   if (s.aggr & kAggrWarpMerge) {
     if (s.kw == 1) k_count_emit<1, true><<<(unsigned)(n_sms * kCountBlocksPerSM), kCountThreads, smC, st>>>(s, b);

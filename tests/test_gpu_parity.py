@@ -336,3 +336,39 @@ def test_aggregation_variants_keep_the_result(torch_cuda, no_buckets, merge):
                 assert_parity(c, reads, offsets, k, canonical, f"variant {no_buckets} {merge} k={k}")
     finally:
         c.close()
+
+
+# ---------------------------------------------------------------- sampled fine layout
+def test_sampled_fine_layout(torch_cuda):
+    """Fine partitions' regions sized from a 1/8 sample of the keys (the default for counts of
+    2^26 bases and more) forced on medium inputs: the result equals the oracle's."""
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(test_fine_sampled=True)
+    try:
+        reads, offsets, _ = synth.generate(synth.REPEAT_SHORT, 1002, 0.03)  # 3 M bases
+        assert_parity(c, reads, offsets, 31, True, "sampled k31")
+        assert c.stats()["fine_sampled"] == 1
+        reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.02)  # 20 M bases, 128-bit keys
+        assert_parity(c, reads, offsets, 63, True, "sampled k63")
+        reads, offsets, _ = synth.generate(synth.UNIFORM_SHORT, 1001, 0.5)
+        assert_parity(c, reads, offsets, 21, False, "sampled k21 forward")
+    finally:
+        c.close()
+
+
+def test_sampled_layout_overflow_takes_the_exact_split(torch_cuda):
+    """Regions without slack overflow: the runs past a region's end are not written, the
+    spill is recorded, and the exact fine split that follows gives the oracle's result."""
+    from paper_2505_04431_gb300 import KmerCounter
+    for extra in ({}, {"defer_all": True}):
+        c = KmerCounter(test_fine_sampled=True, test_tight_slack=True, **extra)
+        try:
+            reads, offsets, _ = synth.generate(synth.REPEAT_SHORT, 1002, 0.03)
+            assert_parity(c, reads, offsets, 31, True, f"tight k31 {extra}")
+            st = c.stats()
+            assert st["fine_sampled"] == 1 and st["fine_resplit"] == 1
+            reads, offsets, _ = synth.generate(synth.LONG_NOISY, 1003, 0.02)
+            assert_parity(c, reads, offsets, 63, True, f"tight k63 {extra}")
+            assert c.stats()["fine_resplit"] == 1
+        finally:
+            c.close()
