@@ -325,7 +325,7 @@ kc::ShapeOpts shape_opts(const kc_plan_s* p) {
 }
 
 void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets, uint64_t n_reads, uint64_t L,
-              bool off_dev, int k, int canonical, Job& j, bool stage_host = false, bool single = false) {
+              bool off_dev, int k, int canonical, Job& j, bool stage_host = false, bool sampled_ok = false) {
   j.reads = reads;
   j.offsets = offsets;
   j.n_reads = n_reads;
@@ -336,7 +336,7 @@ void plan_job(const kc_plan_s* p, const uint8_t* reads, const uint64_t* offsets,
   j.stage_r = stage_host && L > 0 && !j.reads_dev;
   j.stage_o = stage_host && !off_dev;
   kc::ShapeOpts o = shape_opts(p);
-  o.allow_sampled = single ? 1 : 0;  // batched counts keep the exact fine layout
+  o.allow_sampled = sampled_ok ? 1 : 0;
   j.nf_max = kc::make_shape(o, L, n_reads, k, canonical, j.copy_reads && !j.stage_r, !off_dev && !j.stage_o, j.s,
                             j.lay);
   j.P1 = 1 << j.s.b1;
@@ -566,6 +566,7 @@ bool plan_groups(const kc_plan_s* p, const std::vector<Job>& jobs, GroupPlan& gp
   return true;
 }
 
+
 // Enqueue one group on the plan's stream: its outputs (two allocations, owned by `o`), the
 // descriptors and block tables staged at `h` (pinned) and copied to `dv`, the input copies,
 // the batched launches, and each count's status record to meta_dst[q].
@@ -597,6 +598,7 @@ bool enqueue_group(kc_plan_s* p, std::vector<Job>& jobs, const Group& g, GroupOw
   bp.n = (int)n;
   bp.kw = jobs[g.idx[0]].s.kw;
   bp.P1_max = P1_max;
+  for (uint32_t q = 0; q < n; ++q) bp.sampled |= jobs[g.idx[q]].s.fine_sampled;
   bp.host = hd;
   bp.desc = (const kc::BatchDesc*)dv;
   const size_t dbytes = align_up(n * sizeof(kc::BatchDesc), 256);
@@ -933,7 +935,7 @@ kc_status kc_count_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const* 
     if (!off_dev && (offsets[i][0] != 0 || offsets[i][n_reads[i]] != n_bases[i]))  // order: checked on the device
       return fail(KC_EINVAL, "kc_count_batch: a sample's offsets must run from 0 to its base count");
     if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_count_batch: reads of a sample is NULL");
-    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
+    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i], false, true);
   }
   // ---- groups: counts whose scratch fits the arena together share the batched launches
   // (every kernel once per group); a count larger than the arena runs alone
@@ -1153,7 +1155,7 @@ kc_status kc_submit_batch(kc_plan_t p, uint32_t n_samples, const uint8_t* const*
         if (offsets[i][r + 1] < offsets[i][r]) return fail(KC_EINVAL, "kc_submit_batch: offsets must be non-decreasing");
     }
     if (n_bases[i] > 0 && !reads[i]) return fail(KC_EINVAL, "kc_submit_batch: reads of a sample is NULL");
-    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i]);
+    plan_job(p, reads[i], offsets[i], n_reads[i], n_bases[i], off_dev, k, canonical, jobs[i], false, true);
   }
   GroupPlan gp;
   std::string err;

@@ -146,6 +146,7 @@ struct BatchPlan {
   int n = 0;
   int kw = 1;
   int P1_max = 1;
+  int sampled = 0;                  // some count has a sampled fine layout (the exact split may follow)
   const BatchDesc* host = nullptr;  // n descriptors
   const BatchDesc* desc = nullptr;  // device copy
   // per kernel: device block->count table and block starts (n + 1), and the grid

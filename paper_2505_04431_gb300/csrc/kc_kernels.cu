@@ -1087,9 +1087,9 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist(Shape s, Buffers 
   fine_hist_body<KW>(s, b, blockIdx.x, gridDim.x, redo != 0);
 }
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t) {
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_hist_batch(BatchTab t, int redo) {
   KC_BATCH_PROLOGUE(t);
-  fine_hist_body<KW>(d.s, d.b, bid, nblk);
+  fine_hist_body<KW>(d.s, d.b, bid, nblk, redo != 0);
 }
 
 // Keys at positions below x of the keys array that a sampled fine histogram counts: one
@@ -1181,9 +1181,15 @@ __global__ void k_fine_redo_clear(Shape sh, Buffers b) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < sh.nf_max; i += (uint64_t)gridDim.x * blockDim.x)
     b.fhist[i] = 0;
 }
-__global__ void k_fine_scan_batch(BatchTab t) {
+__global__ void k_fine_scan_batch(BatchTab t, int redo) {
   KC_BATCH_PROLOGUE(t);
-  fine_scan_body(d.s, d.b);
+  fine_scan_body(d.s, d.b, redo != 0);
+}
+// (the fine scan's table: one block per count)
+__global__ void k_fine_redo_clear_batch(BatchTab t) {
+  KC_BATCH_PROLOGUE(t);
+  if (!d.b.meta->fine_spill) return;
+  for (uint64_t i = threadIdx.x; i < d.s.nf_max; i += blockDim.x) d.b.fhist[i] = 0;
 }
 
 // Exclusive scan of in[0, n) into out[0, n) (all threads of the block, n <= 4 * blockDim);
@@ -1336,9 +1342,9 @@ __global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter(Shape s, Buffe
   fine_scatter_body<KW>(s, b, blockIdx.x, gridDim.x, redo != 0);
 }
 template <int KW>
-__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter_batch(BatchTab t) {
+__global__ void __launch_bounds__(kFineThreads, 2) k_fine_scatter_batch(BatchTab t, int redo) {
   KC_BATCH_PROLOGUE(t);
-  fine_scatter_body<KW>(d.s, d.b, bid, nblk);
+  fine_scatter_body<KW>(d.s, d.b, bid, nblk, redo != 0);
 }
 
 // ------------------------------------------------------------------ phase 2: count + emit
@@ -2501,26 +2507,36 @@ int launch_batch(const BatchPlan& bp, int n_sms, void* stream, const Marker& mar
   }
   KC_BLAUNCH(BK_FINE_PLAN, (k_fine_plan_batch<<<bp.grid[BK_FINE_PLAN], 1024, (size_t)P1 * 8, st>>>(tab(BK_FINE_PLAN))),
              "k_fine_plan");
-  if (bp.kw == 1) {
-    KC_BLAUNCH(BK_FINE_HIST,
-               (k_fine_hist_batch<1><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
-               "k_fine_hist");
-  } else {
-    KC_BLAUNCH(BK_FINE_HIST,
-               (k_fine_hist_batch<2><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(tab(BK_FINE_HIST))),
-               "k_fine_hist");
-  }
-  KC_BLAUNCH(BK_FINE_SCAN, (k_fine_scan_batch<<<bp.grid[BK_FINE_SCAN], 1024, 0, st>>>(tab(BK_FINE_SCAN))), "k_fine_scan");
-  if (bp.kw == 1) {
-    KC_BLAUNCH(BK_FINE_SCATTER,
-               (k_fine_scatter_batch<1><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(1, P1), st>>>(
-                   tab(BK_FINE_SCATTER))),
-               "k_fine_scatter");
-  } else {
-    KC_BLAUNCH(BK_FINE_SCATTER,
-               (k_fine_scatter_batch<2><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(2, P1), st>>>(
-                   tab(BK_FINE_SCATTER))),
-               "k_fine_scatter");
+  // the fine split; then, for counts with a sampled layout, the exact split again (each
+  // count's blocks return at once unless its sampled regions overflowed)
+  for (int redo = 0; redo <= (bp.sampled ? 1 : 0); ++redo) {
+    if (redo)
+      KC_BLAUNCH(BK_FINE_SCAN, (k_fine_redo_clear_batch<<<bp.grid[BK_FINE_SCAN], 1024, 0, st>>>(tab(BK_FINE_SCAN))),
+                 "k_fine_redo_clear");
+    if (bp.kw == 1) {
+      KC_BLAUNCH(BK_FINE_HIST,
+                 (k_fine_hist_batch<1><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(
+                     tab(BK_FINE_HIST), redo)),
+                 redo ? "k_fine_hist_redo" : "k_fine_hist");
+    } else {
+      KC_BLAUNCH(BK_FINE_HIST,
+                 (k_fine_hist_batch<2><<<bp.grid[BK_FINE_HIST], kFineThreads, fine_hist_smem(P1), st>>>(
+                     tab(BK_FINE_HIST), redo)),
+                 redo ? "k_fine_hist_redo" : "k_fine_hist");
+    }
+    KC_BLAUNCH(BK_FINE_SCAN, (k_fine_scan_batch<<<bp.grid[BK_FINE_SCAN], 1024, 0, st>>>(tab(BK_FINE_SCAN), redo)),
+               redo ? "k_fine_scan_redo" : "k_fine_scan");
+    if (bp.kw == 1) {
+      KC_BLAUNCH(BK_FINE_SCATTER,
+                 (k_fine_scatter_batch<1><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(1, P1), st>>>(
+                     tab(BK_FINE_SCATTER), redo)),
+                 redo ? "k_fine_scatter_redo" : "k_fine_scatter");
+    } else {
+      KC_BLAUNCH(BK_FINE_SCATTER,
+                 (k_fine_scatter_batch<2><<<bp.grid[BK_FINE_SCATTER], kFineThreads, fine_scatter_smem(2, P1), st>>>(
+                     tab(BK_FINE_SCATTER), redo)),
+                 redo ? "k_fine_scatter_redo" : "k_fine_scatter");
+    }
   }
   const size_t smC = count_kernel_smem(bp.kw, s0.bT_max, s0.tail);
   if (bp.kw == 1) {

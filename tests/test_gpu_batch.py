@@ -134,3 +134,25 @@ def test_batch_several_groups_and_counts_alone(counter, torch_cuda, k, canonical
                 assert onv == nv and np.array_equal(keys, ok) and np.array_equal(counts, oc)
     finally:
         small.close()
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_batch_with_sampled_fine_layouts(torch_cuda, tight):
+    """Batched launches over counts whose fine regions are sized from a sample (forced here
+    on small samples) and, without slack, overflow so that the exact split runs for them:
+    every sample equals the oracle."""
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(test_fine_sampled=True, test_tight_slack=tight)
+    try:
+        samples = batch_samples(6, 0.02, seed=2004)
+        samples.insert(2, (np.zeros(0, np.uint8), np.zeros(1, np.uint64)))
+        for k in (31, 63):
+            results = c.count_batch(samples, k, True)
+            for i, ((r, o), res) in enumerate(zip(samples, results)):
+                keys, counts = res.to_numpy()
+                ek, ec, env = oracle.count(r, o, k, True)
+                assert res.n_valid_windows == env, (k, i)
+                assert np.array_equal(keys.reshape(ek.shape), ek) and np.array_equal(counts, ec), f"k {k} sample {i}"
+                res.free()
+    finally:
+        c.close()
