@@ -1303,8 +1303,9 @@ __device__ __forceinline__ void fine_scatter_body(const Shape& s, const Buffers&
         if (v) {
           uint64_t gb = s.cap_kb;  // positions at or past cap_kb are rejected below
           if (g_lo + i < s.nf_max) {
+            const uint64_t lim = sampled ? b.foff[g_lo + i + 1] : ~0ull;  // loaded before the bump
             gb = atomicAdd(&b.fcur[g_lo + i], (unsigned long long)v);
-            if (sampled && gb + v > b.foff[g_lo + i + 1]) {  // the run passes its region's end
+            if (gb + v > lim) {  // the run passes its region's end
               b.meta->fine_spill = 1;
               gb = kSpilledRun;
             }
