@@ -289,6 +289,9 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         for name, ms in pcounter.kernel_times():
             ktimes.setdefault(name, []).append(ms)
     pcounter.close()
+    # the profiling plan's scratch goes back to the driver: what follows measures one plan
+    # alone, as a user holds it, not next to cached blocks of the passes before it
+    torch.cuda.empty_cache()
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     if dist:
         dist.barrier()
@@ -338,6 +341,7 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         if got != D * e2e_steps:
             raise RuntimeError(f"pipelined counts returned {got} entries, expected {D * e2e_steps}")
         keys_h, cnt_h = outs[0]
+        torch.cuda.empty_cache()  # the pipelined run's cached result blocks go back as well
 
         # each serial step timed in its own parts as it runs: the count call (its input copy
         # included) and the result copy, device time by events on the plan's stream and host
@@ -356,7 +360,7 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             ev[2].record(stream)
             t_c = time.perf_counter()
             res.free()
-            steps_parts.append((ev, (t_b - t_a) * 1e3, (t_c - t_b) * 1e3))
+            steps_parts.append((ev, (t_b - t_a) * 1e3, (t_c - t_b) * 1e3, (time.perf_counter() - t_c) * 1e3, t_a))
 
         serial_step()
         torch.cuda.synchronize()
@@ -366,9 +370,12 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             serial_step()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
-        sp = np.array([(ev[0].elapsed_time(ev[1]), wa, ev[1].elapsed_time(ev[2]), wb) for ev, wa, wb in steps_parts])
+        sp = np.array([(ev[0].elapsed_time(ev[1]), wa, ev[1].elapsed_time(ev[2]), wb, wf) for ev, wa, wb, wf, _ in steps_parts])
+        starts = [x[4] for x in steps_parts]
         in_step = {"count_call_device_ms": float(np.median(sp[:, 0])), "count_call_wall_ms": float(np.median(sp[:, 1])),
-                   "copy_out_device_ms": float(np.median(sp[:, 2])), "copy_out_wall_ms": float(np.median(sp[:, 3]))}
+                   "copy_out_device_ms": float(np.median(sp[:, 2])), "copy_out_wall_ms": float(np.median(sp[:, 3])),
+                   "free_wall_ms": float(np.median(sp[:, 4])),
+                   "step_wall_ms": float(np.median(np.diff(starts)) * 1e3) if len(starts) > 1 else None}
         # the serial step's parts apart, host wall clock around each with the stream drained:
         # the inputs in (the same pinned buffers), the count on those device inputs, the result out
         rd = torch.empty_like(r_pin, device=dev)
