@@ -315,6 +315,23 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         outs = [(torch.empty(max(1, D * kw), dtype=torch.int64).pin_memory(),
                  torch.empty(max(1, D), dtype=torch.int32).pin_memory()) for _ in range(2)]
 
+        def link_probe():
+            """The host link as it is now: the reads copied in from and out to their pinned
+            buffer (the device copy holds the same bytes), best of two, on the plan's stream."""
+            out = {}
+            for name, dst, src in (("h2d", r_dev, r_pin), ("d2h", r_pin, r_dev)):
+                best = float("inf")
+                for _ in range(2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        e0.record(stream)
+                        dst.copy_(src, non_blocking=True)
+                        e1.record(stream)
+                    stream.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                out[name] = L / best / 1e6
+            return out
+
         def pipelined(n):
             jobs = collections.deque()
             got = 0
@@ -333,6 +350,7 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             return got
 
         e2e_steps = max(3, min(args.steps, 10))
+        link_before = link_probe()
         pipelined(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -400,6 +418,7 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         parts = {"h2d_ms": float(med[0]), "count_ms": float(med[1]), "d2h_ms": float(med[2])}
         parts["rest_ms"] = dt * 1e3 / e2e_steps - sum(parts.values())
         del rd, od
+        link_after = link_probe()
         h2d_bytes = int(L + 8 * (n_reads + 1))
         d2h_bytes = int(D * (8 * kw + 4))
         e2e = {"value": whole_job_rate(K, world, e2e_steps, dt_pipe * 1e3), "unit": UNIT,
@@ -411,9 +430,18 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
                           "form": "kc_count (pinned host reads) + kc_result_copy_to_host, one step at a time",
                           "parts": parts, "in_step": in_step,
                           "link_gbs": {"h2d": h2d_bytes / parts["h2d_ms"] / 1e6,
-                                       "d2h": d2h_bytes / max(parts["d2h_ms"], 1e-9) / 1e6}}}
+                                       "d2h": d2h_bytes / max(parts["d2h_ms"], 1e-9) / 1e6}},
+               "link_probe_gbs": {"before": link_before, "after": link_after,
+                                  "what": f"the {L / 1e9:.2f} GB of reads copied in and out alone, best of two, "
+                                          "before the pipelined run and after the serial one"}}
+        del r_pin, o_pin, outs, keys_h, cnt_h
 
     counter.close()
+    # pinned host buffers cached by torch go back to the system too, so that the next
+    # workload's end-to-end run does not sit beside them
+    torch.cuda.synchronize()
+    if hasattr(torch._C, "_host_emptyCache"):
+        torch._C._host_emptyCache()
     if rank != 0:
         return None
     w = 8 * kw
