@@ -277,21 +277,6 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     stats = counter.stats()
-    # per-kernel split: the same steps on a plan that records a CUDA event on its stream after
-    # every launch (a separate pass, so that the timed steps above run the plain product path)
-    pstream = torch.cuda.Stream(dev)
-    pcounter = KmerCounter(device=dev, stream=pstream, profile=True)
-    step(pcounter)
-    ktimes = {}
-    prof_steps = max(3, min(args.steps, 5))
-    for _ in range(prof_steps):
-        step(pcounter)
-        for name, ms in pcounter.kernel_times():
-            ktimes.setdefault(name, []).append(ms)
-    pcounter.close()
-    # the profiling plan's scratch goes back to the driver: what follows measures one plan
-    # alone, as a user holds it, not next to cached blocks of the passes before it
-    torch.cuda.empty_cache()
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     if dist:
         dist.barrier()
@@ -303,7 +288,9 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
     # kc_job_copy_to_host of each result into pinned host buffers (copied out there as soon as
     # the count ends), two counts in flight, so that the copies of one step overlap the
     # counting of the next.  Serial (reported beside it): kc_count with the host buffers, then
-    # kc_result_copy_to_host, one step at a time, with its parts timed apart.
+    # kc_result_copy_to_host, one step at a time, with its parts timed apart.  Both run on the
+    # plan of the timed steps, before the profiled pass: a plan in steady use, its scratch and
+    # result blocks already held by the caching allocator.
     e2e = None
     if with_e2e and not args.no_e2e:
         import collections
@@ -350,8 +337,9 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             return got
 
         e2e_steps = max(3, min(args.steps, 10))
+        e2e_warmup = max(3, args.warmup)
         link_before = link_probe()
-        pipelined(2)
+        pipelined(e2e_warmup)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         got = pipelined(e2e_steps)
@@ -359,7 +347,6 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         if got != D * e2e_steps:
             raise RuntimeError(f"pipelined counts returned {got} entries, expected {D * e2e_steps}")
         keys_h, cnt_h = outs[0]
-        torch.cuda.empty_cache()  # the pipelined run's cached result blocks go back as well
 
         # each serial step timed in its own parts as it runs: the count call (its input copy
         # included) and the result copy, device time by events on the plan's stream and host
@@ -380,7 +367,8 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
             res.free()
             steps_parts.append((ev, (t_b - t_a) * 1e3, (t_c - t_b) * 1e3, (time.perf_counter() - t_c) * 1e3, t_a))
 
-        serial_step()
+        for _ in range(e2e_warmup):
+            serial_step()
         torch.cuda.synchronize()
         steps_parts.clear()
         t0 = time.perf_counter()
@@ -437,6 +425,20 @@ def measure(workload, args, dist=None, world=1, rank=0, dev=0, with_e2e=True, wi
         del r_pin, o_pin, outs, keys_h, cnt_h
 
     counter.close()
+    torch.cuda.empty_cache()
+    # per-kernel split: the same steps on a plan that records a CUDA event on its stream after
+    # every launch (a separate pass, so that the timed steps above run the plain product path)
+    pstream = torch.cuda.Stream(dev)
+    pcounter = KmerCounter(device=dev, stream=pstream, profile=True)
+    step(pcounter)
+    ktimes = {}
+    prof_steps = max(3, min(args.steps, 5))
+    for _ in range(prof_steps):
+        step(pcounter)
+        for name, ms in pcounter.kernel_times():
+            ktimes.setdefault(name, []).append(ms)
+    pcounter.close()
+    torch.cuda.empty_cache()
     # pinned host buffers cached by torch go back to the system too, so that the next
     # workload's end-to-end run does not sit beside them
     torch.cuda.synchronize()
