@@ -205,8 +205,7 @@ kc_status kc_last_kernel_times(kc_plan_t plan, uint32_t max, const char **names,
  * Alignment: offsets 8 bytes, out_counts 4 bytes, out_keys 8 bytes (16 bytes for k > 32);
  * a misaligned buffer is refused on the host before anything is launched.
  * The first call on a device (with that device current) looks up the scratch array's
- * device address and sets kernel attributes; make that first call before any stream
- * capture.  Every call reads the offsets and its status record back, so it synchronises
+ * device address and sets kernel attributes.  Every call reads the offsets and its status record back, so it synchronises
  * its stream.  All calls share the one array, and each call clears what it needs: calls
  * that overlap on the GPU (other streams, other host threads) race and must not be made.
  * Errors: KC_EINVAL (sizes beyond the maximum, host or misaligned buffers, small

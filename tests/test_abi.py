@@ -39,10 +39,10 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_library_is_built_for_sm103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", kcpy.LIB_PATH], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    """Every compile and the link take the one sm_103a target and no other architecture."""
+    from paper_2505_04431_gb300 import build as kcbuild
+    assert kcbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert not any(f.startswith(("-gencode", "-arch", "--gpu-architecture", "-code")) for f in kcbuild.FLAGS)
 
 
 def test_host_side_argument_errors(lib):
