@@ -137,3 +137,43 @@ def test_unordered_host_offsets_are_reported_when_collected(counter, torch_cuda)
     keys, counts = res.to_numpy()
     res.free()
     assert np.array_equal(keys, ak) and np.array_equal(counts, ac)
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_pipelined_counts_with_sampled_fine_layouts(counter, torch_cuda, tight):
+    """Submitted host counts on a plan that sizes fine partition regions from a sample at
+    every size (with `tight`, with no slack, so that regions spill and the exact fine split
+    runs inside the job): every result copied out equals the plain plan's count alone."""
+    torch = torch_cuda
+    from paper_2505_04431_gb300 import KmerCounter
+    c = KmerCounter(test_fine_sampled=True, test_tight_slack=tight)
+    try:
+        inputs = [synth.generate(synth.REPEAT_SHORT, 1002, 0.03)[:2],  # 3 M bases
+                  synth.generate(synth.LONG_NOISY, 1003, 0.02)[:2],  # 20 M bases, 128-bit keys
+                  synth.generate(synth.SERVE, synth.mix_seed(1007, 0), 0.03)[:2],
+                  synth.generate(synth.SERVE, synth.mix_seed(1007, 1), 0.03)[:2]]
+        ks = [31, 63, 21, 31]
+        jobs, outs, got = [], [], []
+        for (r, o), k in zip(inputs, ks):
+            j = c.submit(r, o, k, True, n_bases=int(o[-1]))
+            out = host_out(torch, max(1, len(r)), k)
+            c.copy_to_host(j, *out)
+            jobs.append(j)
+            outs.append(out)
+        resplit = 0
+        for j in jobs:
+            res = c.wait(j)
+            got.append((res.n, res.n_valid_windows))
+            resplit += c.stats()["fine_resplit"]
+            res.free()
+        for i, ((r, o), k) in enumerate(zip(inputs, ks)):
+            ak, ac, an, anv = alone(counter, r, o, k)
+            n, nv = got[i]
+            kw = 1 if k <= 32 else 2
+            assert n == an and nv == anv, f"input {i}"
+            assert np.array_equal(outs[i][0][: n * kw].numpy().view(np.uint64), ak.reshape(-1)), f"input {i} keys"
+            assert np.array_equal(outs[i][1][:n].numpy().view(np.uint32), ac), f"input {i} counts"
+        if tight:
+            assert resplit > 0, "no region spilled with tight slack"
+    finally:
+        c.close()
