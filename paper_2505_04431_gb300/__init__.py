@@ -260,6 +260,7 @@ class KmerCounter:
         self._opts = opts
         self._plan = plan
         self._inflight = {}  # job id -> the buffers it reads
+        self._job_kw = {}  # job id -> its key words (1 for k <= 32, else 2)
 
     def count(self, reads, offsets, k: int, canonical: bool = True) -> CountResult:
         """Sorted (k-mer, count) histogram of the reads (host or device buffers)."""
@@ -317,6 +318,7 @@ class KmerCounter:
         _check(self._lib, self._lib.kc_submit(self._plan, rp, op, n_reads, int(n_bases), int(k),
                                               int(bool(canonical)), ctypes.byref(job)))
         self._inflight[job.value] = (rk, ok)
+        self._job_kw[job.value] = 1 if int(k) <= 32 else 2
         return job.value
 
     def submit_batch(self, samples, k: int, canonical: bool = True) -> list[int]:
@@ -347,20 +349,35 @@ class KmerCounter:
         out = [int(jobs[i]) for i in range(n)]
         for j, kept in zip(out, keep):
             self._inflight[j] = kept
+            self._job_kw[j] = 1 if int(k) <= 32 else 2
         return out
 
     def copy_to_host(self, job: int, keys_host, counts_host) -> None:
         """Have a submitted job's result copied to host buffers as soon as its count ends
         (kc_job_copy_to_host): keys_host holds capacity x key words (int64/uint64), counts_host
         capacity counts (int32/uint32); pinned memory lets the copy overlap later counts.
-        The job is reported done once the copy has completed."""
+        The job is reported done once the copy has completed.  The buffers are checked here
+        against the job's key width, as the C call takes plain pointers."""
         for x in (keys_host, counts_host):
             ok = x.flags["C_CONTIGUOUS"] if isinstance(x, np.ndarray) else x.is_contiguous()
             if not ok:
                 raise ValueError("copy_to_host: the host buffers must be contiguous")
+
+        def size(x):  # (elements, bytes per element)
+            if isinstance(x, np.ndarray):
+                return x.size, x.itemsize
+            return x.numel(), x.element_size()
+
+        nk, sk = size(keys_host)
+        nc, sc = size(counts_host)
+        if sk != 8 or sc != 4:
+            raise ValueError("copy_to_host: keys_host takes 64-bit words, counts_host 32-bit counts")
+        cap = nc
+        kw = self._job_kw.get(int(job))
+        if kw is not None and nk < cap * kw:
+            raise ValueError(f"copy_to_host: keys_host holds {nk} words; {cap} keys of this job take {cap * kw}")
         kp, kk = _ptr(keys_host)
         cp, ck = _ptr(counts_host)
-        cap = counts_host.shape[0] if hasattr(counts_host, "shape") else len(counts_host)
         _check(self._lib, self._lib.kc_job_copy_to_host(self._plan, int(job), kp, cp, int(cap)))
         self._inflight[int(job)] = self._inflight.get(int(job), ()) + (kk, ck)
 
@@ -373,6 +390,7 @@ class KmerCounter:
         finally:
             if done.value:
                 self._inflight.pop(int(job), None)
+                self._job_kw.pop(int(job), None)
         return CountResult(self, res) if done.value else None
 
     def wait(self, job: int) -> CountResult:
@@ -382,6 +400,7 @@ class KmerCounter:
             _check(self._lib, self._lib.kc_job_wait(self._plan, int(job), ctypes.byref(res)))
         finally:
             self._inflight.pop(int(job), None)
+            self._job_kw.pop(int(job), None)
         return CountResult(self, res)
 
     def footprint(self, n_reads: int, n_bases: int, k: int, reads_on_device: bool = True,
@@ -415,6 +434,7 @@ class KmerCounter:
             self._lib.kc_plan_destroy(self._plan)
             self._plan = None
             self._inflight.clear()
+            self._job_kw.clear()
 
     def __del__(self):
         try:

@@ -177,3 +177,23 @@ def test_pipelined_counts_with_sampled_fine_layouts(counter, torch_cuda, tight):
             assert resplit > 0, "no region spilled with tight slack"
     finally:
         c.close()
+
+
+def test_copy_to_host_checks_the_buffers_against_the_job(counter, torch_cuda):
+    """The binding refuses host buffers whose element sizes, or whose key words for the job's
+    k, do not fit, before the C call takes their plain pointers; the job is then collected
+    as usual."""
+    torch = torch_cuda
+    r, o, _ = synth.generate(synth.SERVE, synth.mix_seed(1006, 13), 0.01)
+    cap = max(1, len(r))
+    job = counter.submit(r, o, 63, True, n_bases=int(o[-1]))
+    with pytest.raises(ValueError):  # one word per key, where k = 63 keys take two
+        counter.copy_to_host(job, torch.empty(cap, dtype=torch.int64), torch.empty(cap, dtype=torch.int32))
+    with pytest.raises(ValueError):  # 64-bit counts
+        counter.copy_to_host(job, torch.empty(2 * cap, dtype=torch.int64), torch.empty(cap, dtype=torch.int64))
+    res = counter.wait(job)
+    keys, counts = res.to_numpy()
+    n = res.n
+    res.free()
+    ak, ac, an, _ = alone(counter, r, o, 63)
+    assert n == an and np.array_equal(keys, ak) and np.array_equal(counts, ac)
